@@ -1,0 +1,23 @@
+"""CPU oracle for approximate tensor-network contraction (test infrastructure).
+
+Plain, slow, FP64 numpy restatement of what the GPU library computes, used
+only by the tests, by ``__graft_entry__.smoke()`` and by the CPU-baseline leg
+of ``bench.py``.  The product path never imports it.  It shares no code with
+the CUDA library: both sides only read the same network and tree files
+written by ``tn_inputs``.
+
+Modules:
+  approx  -- Algorithm 1 over an explicit ordered tree: pairwise contraction
+             (Eq. 1 as a matrix product over the shared bonds) and bond
+             compression (QR of A, LQ of B, SVD of R_A R_B truncated to chi,
+             sqrt(sigma) absorbed into both sides; Eq. "svd"), with an exact
+             power-of-two running log-norm.
+  exact   -- independent references: brute-force sums over spin / edge
+             configurations, row transfer matrices, closed forms, perfect
+             matching counts, and full einsum contraction of tiny networks.
+  grad    -- d log|Z| / d T by reverse-mode differentiation of the same
+             executor written in plain PyTorch CPU float64 ops.
+
+Every function states the passage of the paper it follows.  Where the paper
+is silent the reading used is stated in the docstring.
+"""

@@ -1,0 +1,391 @@
+"""Ordered approximate contraction tree generators (host side, plain Python).
+
+A tree is independent of the tensor entries, so one tree serves a whole beta
+sweep or every seed of a random ensemble.  Generators:
+
+* ``boundary_rows``: the hand-coded boundary contraction of a 2D lattice
+  (rows absorbed from the bottom, then the bonds between neighbouring
+  boundary tensors compressed left to right after each row).
+* ``from_pairs``: any sequence of pairwise contractions, with explicit
+  compressions inserted either after each contraction ("early") or before it
+  ("late"), following the two policies of Algorithm 1.
+* ``greedy``: the Greedy builder of the SI (local score from the sizes before
+  and after compression, input sizes, sub-graph sizes, centrality and a
+  Gumbel noise term), simulated with chi_greedy.
+
+The shape simulation here only decides an order; it never touches tensor
+entries.  A compression of the bonds shared by A and B yields one bond of
+size min(chi, D_A, D_B) when the shared size D_AB exceeds chi.
+"""
+from __future__ import annotations
+
+import heapq
+import math
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from .formats import Network, Tree
+
+# ---------------------------------------------------------------------------
+# fixed orders
+
+
+def boundary_rows(lx: int, ly: int) -> Tree:
+    """Row-by-row boundary order for ``networks.square_lattice(lx, ly)`` ids.
+
+    Row 0 is the initial boundary.  For each next row, site (x, y) is
+    contracted into boundary tensor x for x = 0..lx-1, then S ops compress
+    the bonds between boundary tensors (0,1), (1,2), ... left to right.
+    Finally the boundary is contracted left to right into one scalar.
+    """
+    n = lx * ly
+    nxt = n
+    ops: List[tuple] = []
+    b = list(range(lx))
+    for y in range(1, ly):
+        for x in range(lx):
+            ops.append(("C", b[x], y * lx + x, nxt))
+            b[x] = nxt
+            nxt += 1
+        if lx > 1:
+            for x in range(lx - 1):
+                ops.append(("S", b[x], b[x + 1]))
+    acc = b[0]
+    for x in range(1, lx):
+        ops.append(("C", acc, b[x], nxt))
+        acc = nxt
+        nxt += 1
+    return Tree(n, ops)
+
+
+def _neighbours(bonds: Dict[int, List[int]], bond_owner: Dict[int, List[int]], t: int) -> List[int]:
+    out = set()
+    for b in bonds[t]:
+        for o in bond_owner[b]:
+            if o != t:
+                out.add(o)
+    return sorted(out)
+
+
+def from_pairs(net_bonds: Sequence[Sequence[int]], pairs: Sequence[Tuple[int, int]],
+               policy: str = "early") -> Tree:
+    """Emit C ops for ``pairs`` (ids refer to live tensors; new ids are
+    allocated in order) and S ops around them.
+
+    early: after C i j -> k, S k l for every neighbour l of k, ascending l.
+    late:  before C i j, S i l for every neighbour l != j of i (ascending),
+           then S j l for every neighbour l != i of j.
+    S ops whose shared size is <= chi are skipped at run time, so the same
+    tree serves every chi.
+    """
+    n = len(net_bonds)
+    bonds: Dict[int, List[int]] = {t: list(b) for t, b in enumerate(net_bonds)}
+    owner: Dict[int, List[int]] = {}
+    for t, bl in bonds.items():
+        for b in bl:
+            owner.setdefault(b, []).append(t)
+    nxt = n
+    ops: List[tuple] = []
+    for i, j in pairs:
+        if i not in bonds or j not in bonds or i == j:
+            raise ValueError(f"pair ({i}, {j}) is not two live tensors")
+        if policy == "late":
+            for l in _neighbours(bonds, owner, i):
+                if l != j:
+                    ops.append(("S", i, l))
+            for l in _neighbours(bonds, owner, j):
+                if l != i:
+                    ops.append(("S", j, l))
+        k = nxt
+        nxt += 1
+        ops.append(("C", i, j, k))
+        sj = set(bonds[j])
+        si = set(bonds[i])
+        newb = [b for b in bonds[i] if b not in sj] + [b for b in bonds[j] if b not in si]
+        for b in si & sj:
+            del owner[b]
+        for b in newb:
+            owner[b] = [k if o in (i, j) else o for o in owner[b]]
+        del bonds[i], bonds[j]
+        bonds[k] = newb
+        if policy == "early":
+            for l in _neighbours(bonds, owner, k):
+                ops.append(("S", k, l))
+    return Tree(n, ops)
+
+
+def sequential_pairs(n: int) -> List[Tuple[int, int]]:
+    """Contract tensors 0, 1, 2, ... into one growing tensor."""
+    pairs = []
+    acc = 0
+    nxt = n
+    for t in range(1, n):
+        pairs.append((acc, t))
+        acc = nxt
+        nxt += 1
+    return pairs
+
+
+# ---------------------------------------------------------------------------
+# greedy builder
+
+
+def centrality(n: int, adj: Sequence[Sequence[int]]) -> np.ndarray:
+    """c[v] ~ sum_{u != v} 1/sqrt(d(u, v) + 1), rescaled to [0, 1] (SI, tree builders)."""
+    c = np.zeros(n)
+    for s in range(n):
+        dist = [-1] * n
+        dist[s] = 0
+        q = [s]
+        h = 0
+        while h < len(q):
+            u = q[h]
+            h += 1
+            for w in adj[u]:
+                if dist[w] < 0:
+                    dist[w] = dist[u] + 1
+                    q.append(w)
+        c[s] = sum(1.0 / math.sqrt(d + 1) for u, d in enumerate(dist) if u != s and d >= 0)
+    lo, hi = c.min(), c.max()
+    return (c - lo) / (hi - lo) if hi > lo else np.zeros(n)
+
+
+class _Sim:
+    """Live tensors with bond sizes, for scoring candidate contractions."""
+
+    def __init__(self, net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int]):
+        self.bonds: Dict[int, List[int]] = {t: list(b) for t, b in enumerate(net_bonds)}
+        self.dim: Dict[int, int] = {b: int(d) for b, d in enumerate(bond_dims)}
+        self.owner: Dict[int, List[int]] = {}
+        for t, bl in self.bonds.items():
+            for b in bl:
+                self.owner.setdefault(b, []).append(t)
+        self.next_bond = len(bond_dims)
+
+    def log2size(self, t: int) -> float:
+        return sum(math.log2(self.dim[b]) for b in self.bonds[t])
+
+    def groups(self, t: int) -> Dict[int, List[int]]:
+        """neighbour -> shared bonds (in t's order)."""
+        g: Dict[int, List[int]] = {}
+        for b in self.bonds[t]:
+            for o in self.owner[b]:
+                if o != t:
+                    g.setdefault(o, []).append(b)
+        return g
+
+    def contract_sizes(self, i: int, j: int, chi: int) -> Tuple[float, float]:
+        """(log2 size before, log2 size after early compression) of the new tensor."""
+        gi, gj = self.groups(i), self.groups(j)
+        before = 0.0
+        after = 0.0
+        li, lj = self.log2size(i), self.log2size(j)
+        nb = set(gi) | set(gj)
+        nb.discard(i)
+        nb.discard(j)
+        tot: Dict[int, float] = {}
+        for src in (gi, gj):
+            for l, bl in src.items():
+                if l in (i, j):
+                    continue
+                tot[l] = tot.get(l, 0.0) + sum(math.log2(self.dim[b]) for b in bl)
+        shared = sum(math.log2(self.dim[b]) for b in gi.get(j, []))
+        lk = li + lj - 2 * shared
+        for l, s in tot.items():
+            before += s
+            if s > math.log2(chi) + 1e-9:
+                other = self.log2size(l) - s
+                after += min(math.log2(chi), lk - s, other)
+            else:
+                after += s
+        return before, after
+
+    def contract(self, i: int, j: int, k: int) -> None:
+        si, sj = set(self.bonds[i]), set(self.bonds[j])
+        newb = [b for b in self.bonds[i] if b not in sj] + [b for b in self.bonds[j] if b not in si]
+        for b in si & sj:
+            del self.owner[b]
+        for b in newb:
+            self.owner[b] = [k if o in (i, j) else o for o in self.owner[b]]
+        del self.bonds[i], self.bonds[j]
+        self.bonds[k] = newb
+
+    def compress(self, i: int, j: int, chi: int) -> bool:
+        sh = [b for b in self.bonds[i] if b in set(self.bonds[j])]
+        dab = 1
+        for b in sh:
+            dab *= self.dim[b]
+        if dab <= chi:
+            return False
+        da = 1
+        for b in self.bonds[i]:
+            if b not in sh:
+                da *= self.dim[b]
+        db = 1
+        for b in self.bonds[j]:
+            if b not in sh:
+                db *= self.dim[b]
+        knew = min(chi, da, db)
+        nb = self.next_bond
+        self.next_bond += 1
+        self.dim[nb] = knew
+        for t in (i, j):
+            out = []
+            placed = False
+            for b in self.bonds[t]:
+                if b in sh:
+                    if not placed:
+                        out.append(nb)
+                        placed = True
+                else:
+                    out.append(b)
+            self.bonds[t] = out
+        for b in sh:
+            del self.owner[b]
+        self.owner[nb] = [i, j]
+        return True
+
+
+def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int,
+           seed: int = 0, temperature: float = 0.0, w_new: float = 1.0, w_old: float = 0.0,
+           w_inputs: float = -1.0, w_subgraph: float = 0.0, w_centrality: float = 0.0,
+           chi_greedy: Optional[int] = None, policy: str = "early") -> Tree:
+    """Greedy ordered tree: repeatedly contract the adjacent pair of lowest score
+
+        score = w_new * log2|k after compression| + w_old * log2|k before|
+              + w_inputs * (log2|i| + log2|j|) + w_subgraph * (|S(i)| + |S(j)|)
+              + w_centrality * (c_i + c_j) / 2 + temperature * Gumbel,
+
+    simulating early compression at chi_greedy (default chi) after each step.
+    Disconnected components are joined by outer products at the end.
+    """
+    chig = chi_greedy or chi
+    rng = np.random.default_rng(seed)
+    n = len(net_bonds)
+    sim = _Sim(net_bonds, bond_dims)
+    adj0 = [sorted(set(o for b in net_bonds[v] for o in sim.owner[b] if o != v)) for v in range(n)]
+    cent = {v: float(c) for v, c in enumerate(centrality(n, adj0))} if w_centrality else {v: 0.0 for v in range(n)}
+    sub = {v: 1 for v in range(n)}
+    pairs: List[Tuple[int, int]] = []
+    ops: List[tuple] = []
+    nxt = n
+    version: Dict[int, int] = {v: 0 for v in range(n)}
+
+    def score(i: int, j: int) -> float:
+        before, after = sim.contract_sizes(i, j, chig)
+        s = w_new * after + w_old * before + w_inputs * (sim.log2size(i) + sim.log2size(j))
+        s += w_subgraph * (sub[i] + sub[j]) + w_centrality * 0.5 * (cent[i] + cent[j])
+        if temperature:
+            s += temperature * float(-math.log(-math.log(rng.uniform(1e-12, 1.0))))
+        return s
+
+    heap: List[Tuple[float, int, int, int, int]] = []
+
+    def push_around(t: int) -> None:
+        for l in sim.groups(t):
+            a, b = (t, l) if t < l else (l, t)
+            heapq.heappush(heap, (score(a, b), a, b, version[a], version[b]))
+
+    for v in range(n):
+        for l in sim.groups(v):
+            if v < l:
+                heapq.heappush(heap, (score(v, l), v, l, 0, 0))
+    while heap:
+        _, i, j, vi, vj = heapq.heappop(heap)
+        if i not in sim.bonds or j not in sim.bonds or version[i] != vi or version[j] != vj:
+            continue
+        k = nxt
+        nxt += 1
+        ops.append(("C", i, j, k))
+        pairs.append((i, j))
+        sim.contract(i, j, k)
+        sub[k] = sub[i] + sub[j]
+        cent[k] = 0.5 * (cent[i] + cent[j])
+        version[k] = 0
+        for l in sorted(sim.groups(k)):
+            ops.append(("S", k, l))
+            if sim.compress(k, l, chig):
+                version[l] += 1
+        push_around(k)
+        for l in sim.groups(k):
+            push_around(l)
+    live = sorted(sim.bonds)
+    acc = live[0] if live else None
+    for t in live[1:]:
+        ops.append(("C", acc, t, nxt))
+        sim.contract(acc, t, nxt)
+        acc = nxt
+        nxt += 1
+    if policy != "early":
+        raise ValueError("greedy emits early compression")
+    return Tree(n, ops)
+
+
+# ---------------------------------------------------------------------------
+# tracing (Sec. "Tree cost functions" of the SI)
+
+
+def trace_cost(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], tree: Tree, chi: int) -> Dict[str, float]:
+    """Walk the tree for one chi and count the paper's cost units
+
+    contraction (m, n) x (n, k): m n k;  QR of (m, n), m >= n: 2 m n^2 - 2/3 n^3;
+    SVD of (m, n), m >= n: 4 m n^2 - 4/3 n^3;  plus peak live memory M (elements)
+    and the largest tensor W.  QR here is of each side of a compression
+    (D_A x D_AB and D_AB x D_B), the SVD of the r_A x r_B core.
+    """
+    sim = _Sim(net_bonds, bond_dims)
+    cost_c = cost_qr = cost_svd = 0.0
+    sizes = {t: 2.0 ** sim.log2size(t) for t in sim.bonds}
+    live = sum(sizes.values())
+    peak = live
+    wmax = max(sizes.values()) if sizes else 0.0
+    n_comp = 0
+
+    def qr(m: float, nn: float) -> float:
+        if m < nn:
+            m, nn = nn, m
+        return 2 * m * nn * nn - 2.0 / 3.0 * nn ** 3
+
+    def svd(m: float, nn: float) -> float:
+        if m < nn:
+            m, nn = nn, m
+        return 4 * m * nn * nn - 4.0 / 3.0 * nn ** 3
+
+    for op in tree.ops:
+        if op[0] == "C":
+            _, i, j, k = op
+            sh = [b for b in sim.bonds[i] if b in set(sim.bonds[j])]
+            dab = 2.0 ** sum(math.log2(sim.dim[b]) for b in sh)
+            m = sizes[i] / dab
+            nn = sizes[j] / dab
+            cost_c += m * dab * nn
+            sim.contract(i, j, k)
+            sizes[k] = m * nn
+            live += sizes[k]
+            peak = max(peak, live)
+            live -= sizes.pop(i) + sizes.pop(j)
+            wmax = max(wmax, sizes[k])
+        else:
+            _, i, j = op
+            sh = [b for b in sim.bonds[i] if b in set(sim.bonds[j])]
+            dab = 2.0 ** sum(math.log2(sim.dim[b]) for b in sh)
+            if dab <= chi:
+                continue
+            da = sizes[i] / dab
+            db = sizes[j] / dab
+            ra, rb = min(da, dab), min(db, dab)
+            cost_qr += qr(da, dab) + qr(dab, db)
+            cost_c += ra * dab * rb
+            cost_svd += svd(ra, rb)
+            kk = min(chi, da, db)
+            cost_c += da * ra * kk + kk * rb * db
+            sim.compress(i, j, chi)
+            live -= sizes[i] + sizes[j]
+            sizes[i] = da * kk
+            sizes[j] = kk * db
+            live += sizes[i] + sizes[j]
+            n_comp += 1
+    return {"contract": cost_c, "qr": cost_qr, "svd": cost_svd,
+            "total": cost_c + cost_qr + cost_svd, "peak": peak, "wmax": wmax,
+            "compressions": n_comp}
