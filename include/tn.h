@@ -1,0 +1,183 @@
+/*
+ * tn.h -- C ABI of the GB300 approximate tensor-network contraction library.
+ *
+ * The library executes a frozen, ordered approximate contraction tree
+ * (Algorithm 1 of Gray & Chan, "Hyper-optimized approximate contraction of
+ * tensor networks with arbitrary geometry", arXiv:2206.07044) on one GPU:
+ *
+ *   C i j k : pairwise contraction of tensors i and j over all their shared
+ *             bonds (Eq. 1 for one pair; Fig. 3B), producing tensor k;
+ *   S i j   : compression of the bonds shared by i and j when the product of
+ *             their sizes D_AB exceeds chi (Sec. "Bond compression strategies"):
+ *             QR of A, LQ of B, truncated SVD of R_A R_B to
+ *             k = min(chi, D_A, D_B) singular values, sqrt(sigma) absorbed on
+ *             both sides (Eq. "svd"), applied in the equivalent projector form
+ *             A P_L, P_R B of the SI section "Explicit projector form".
+ *
+ * A power-of-two running log-norm keeps every intermediate in range, so log|Z|
+ * never overflows.  All arithmetic runs in CUDA kernels on the GPU; there is
+ * no CPU fallback.
+ *
+ * Conventions
+ *   - Every function returns a tn_status (0 = TN_OK).  No exception crosses
+ *     the ABI.  On error, tn_last_error() describes the failure.
+ *   - Pointers are host pointers unless stated otherwise.  The library copies
+ *     what it keeps; the caller keeps ownership of everything it passes in.
+ *   - A context lives on one CUDA device and owns the device memory it
+ *     allocates.  Calls are not thread-safe on one context.
+ *   - Work is issued on the context's stream (tn_set_stream; default: the
+ *     legacy default stream) and calls that return results synchronise it.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tn_ctx tn_ctx;
+
+typedef enum {
+  TN_OK = 0,
+  TN_EINVAL = -1,      /* bad argument (null pointer, chi < 1, unknown id, ...) */
+  TN_EFORMAT = -2,     /* malformed network or tree (file or descriptor)        */
+  TN_ESHAPE = -3,      /* shapes disagree (bond listed != twice, data size, ...) */
+  TN_ENOMEM = -4,      /* device or host allocation failed                      */
+  TN_ECUDA = -5,       /* a CUDA runtime call or kernel launch failed           */
+  TN_ETIMEOUT = -6,    /* a bounded device-side wait ran out                    */
+  TN_ENONFINITE = -7,  /* NaN or Inf in input tensor data                       */
+  TN_ESTATE = -8,      /* call out of order (e.g. no tree loaded)               */
+  TN_ENOCONV = -9      /* an iterative kernel (Jacobi SVD) did not converge     */
+} tn_status;
+
+/* Arithmetic form of the contraction and absorb GEMMs.  QR/LQ and the SVD of
+ * the R_A L_B core are FP64 in every form. */
+typedef enum {
+  TN_F64 = 0,    /* every step in FP64 (the plain form)                          */
+  TN_TF32 = 1,   /* GEMMs on tcgen05 tensor cores, TF32 inputs, FP32 accumulate  */
+  TN_BF16 = 2,   /* GEMMs on tcgen05 tensor cores, BF16 inputs, FP32 accumulate  */
+  TN_TF32X3 = 3  /* split-TF32 GEMMs (3 tcgen05 products), near-FP32 accuracy    */
+} tn_prec;
+
+/* A closed tensor network (Eq. 1 with no open indices).
+ *   n_bonds      number of bonds; bond b has size bond_dims[b] >= 1
+ *   n_tensors    number of tensors
+ *   ndims[t]     number of bonds of tensor t (0 allowed: a scalar tensor)
+ *   bond_ids     concatenation over t of tensor t's bond ids, in storage order;
+ *                every bond id must appear in exactly two different tensors
+ *   data[t]      host pointer to tensor t's FP64 entries, row-major over its
+ *                listed bond order (prod of its bond sizes elements)        */
+typedef struct {
+  int32_t n_bonds;
+  const int64_t* bond_dims;
+  int32_t n_tensors;
+  const int32_t* ndims;
+  const int32_t* bond_ids;
+  const double* const* data;
+} tn_network_desc;
+
+/* An ordered approximate contraction tree (Fig. 2B/C).
+ *   n_inputs     must equal the network's n_tensors
+ *   ops          n_ops rows of 4 int32: {0, i, j, k} = C i j k, {1, i, j, -1} = S i j
+ *                Ids 0..n_inputs-1 are the network tensors; the m-th C op must
+ *                create id n_inputs + m.  The ops must reduce the network to
+ *                scalars (every tensor contracted, last op a C).             */
+typedef struct {
+  int32_t n_inputs;
+  int32_t n_ops;
+  const int32_t* ops;
+} tn_tree_desc;
+
+/* Algorithmic work of one instance at one chi (the SI's cost-tracer units,
+ * counted on the schedule the library executes).                            */
+typedef struct {
+  int64_t n_contractions;     /* C ops                                         */
+  int64_t n_compressions;     /* S ops that run at this chi                    */
+  double gemm_flops;          /* 2 m n k over contraction, core and absorb GEMMs */
+  double qr_flops;            /* Householder 2 m n^2 - 2/3 n^3 per factored side */
+  double svd_flops;           /* 4 m n^2 - 4/3 n^3 per core SVD (the SI's count) */
+  double permute_bytes;       /* bytes read + written by permutes              */
+  double peak_bytes;          /* device arena bytes for one instance           */
+  int64_t kernel_launches;    /* kernels per evaluation of this instance       */
+} tn_plan_stats;
+
+/* Create a context on CUDA device `device`.  *out receives the context. */
+int tn_create(tn_ctx** out, int device);
+
+/* Destroy a context and free its device memory.  NULL is ignored. */
+void tn_destroy(tn_ctx* ctx);
+
+/* Issue all later work on `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream).  The stream must belong to the context's device. */
+int tn_set_stream(tn_ctx* ctx, void* cuda_stream);
+
+/* Copy a network into the context (host data -> device).  Validates that each
+ * bond appears in exactly two tensors and that entries are finite
+ * (TN_ENONFINITE otherwise).  *net_id receives the network's id. */
+int tn_load_network(tn_ctx* ctx, const tn_network_desc* desc, int* net_id);
+
+/* Same, from a TNNET1 file (format documented in tn_inputs/formats.py). */
+int tn_load_network_file(tn_ctx* ctx, const char* path, int* net_id);
+
+/* Replace the entries of a loaded network with new values of the same shapes
+ * (e.g. the next beta of a sweep).  data[t] are host pointers when
+ * on_device == 0, device pointers on the context's device otherwise.
+ * Host data is copied with cudaMemcpyAsync on the context's stream and the
+ * call returns once the copy has been issued (host buffers must stay valid
+ * until the next synchronising call). */
+int tn_set_network_data(tn_ctx* ctx, int net_id, const double* const* data, int on_device);
+
+/* Attach an ordered tree to a loaded network, creating an instance (a
+ * network + tree pair).  The tree is validated against the network's shapes
+ * (TN_EFORMAT on a malformed op sequence).  *inst_id receives the instance. */
+int tn_load_tree(tn_ctx* ctx, int net_id, const tn_tree_desc* desc, int* inst_id);
+
+/* Same, from a "tntree 1" text file. */
+int tn_load_tree_file(tn_ctx* ctx, int net_id, const char* path, int* inst_id);
+
+/* Approximately contract n_inst instances at bond dimension chi (>= 1) in the
+ * given arithmetic form.  Instances with identical network structure and tree
+ * run as one batch.  logabsz_out[n] = ln|Z_n| (-inf when Z_n == 0) and
+ * sign_out[n] in {-1, 0, +1} are caller-allocated host arrays of n_inst.
+ * Synchronises the context's stream before returning. */
+int tn_contract_approx(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, int prec,
+                       double* logabsz_out, int* sign_out);
+
+/* Schedule statistics of one instance at chi (no GPU work). */
+int tn_plan_stats_get(tn_ctx* ctx, int inst_id, int chi, int prec, tn_plan_stats* out);
+
+/* Diagnostic: run the batch inst_ids[0..n_inst) exactly as tn_contract_approx
+ * would (same plan, same launches) but stop after the steps of tree op
+ * `stop_op` (0-based op index; -1 = before any op), then copy tensor
+ * `tensor_id` of instance inst_ids[which] to host `out` (cap doubles),
+ * row-major over its storage order.  *ndim_out receives its number of bonds,
+ * bond_ids_out / dims_out (24 entries each, may be NULL) the bond ids and
+ * sizes in storage order; bond ids >= the network's n_bonds are bonds created
+ * by compressions, numbered in execution order.  out == NULL queries the
+ * shape only and runs nothing.  TN_EINVAL if the tensor does not exist after
+ * that op.  Intermediates carry the running power-of-two scale, so values
+ * equal the exact ones up to a factor 2^e. */
+int tn_debug_tensor(tn_ctx* ctx, int n_inst, const int* inst_ids, int which, int chi, int prec,
+                    int stop_op, int tensor_id, double* out, int64_t cap, int32_t* ndim_out,
+                    int32_t* bond_ids_out, int64_t* dims_out);
+
+/* Time every kernel of the next tn_contract_approx with CUDA events, grouped
+ * by kernel family, when enable != 0 (off by default; adds one event pair per
+ * launch).  tn_kernel_times copies up to `cap` entries of (family name,
+ * launches, total milliseconds) and returns the number of families. */
+int tn_profile_enable(tn_ctx* ctx, int enable);
+int tn_kernel_times(tn_ctx* ctx, int cap, const char** names, int64_t* launches, double* total_ms);
+
+/* Message for the last non-OK status returned on this context (never NULL). */
+const char* tn_last_error(const tn_ctx* ctx);
+
+/* Library version string. */
+const char* tn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

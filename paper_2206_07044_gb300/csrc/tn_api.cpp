@@ -1,0 +1,707 @@
+// C ABI (include/tn.h): contexts, network / tree loading and validation,
+// batching of instances, and the step executor that launches the kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <sstream>
+#include <string>
+#include <tuple>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/tn.h"
+#include "tn_kernels.h"
+#include "tn_plan.h"
+
+namespace {
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+struct NetRec {
+  tnp::Structure st;
+  double* d_data = nullptr;
+  uint64_t hash = 0;
+};
+
+struct InstRec {
+  int net = -1;
+  int n_inputs = 0;
+  std::vector<int32_t> ops;
+  uint64_t hash = 0;  // structure + tree
+};
+
+struct PlanKey {
+  uint64_t hash;
+  int chi, prec;
+  bool operator<(const PlanKey& o) const {
+    return std::tie(hash, chi, prec) < std::tie(o.hash, o.chi, o.prec);
+  }
+};
+
+struct CachedPlan {
+  int inst_proto;  // instance whose structure/tree built the plan (for exact equality checks)
+  tnp::Plan plan;
+};
+
+const char* kFamily[] = {"permute", "gemm_f64", "qr_f64", "jacobi_f64", "select_scale", "rescale",
+                         "finalize", "to_f32", "jacobi_f32", "to_f64", "copy", "apply_q_f64"};
+constexpr int kNumFamily = tnp::kNumStepKinds;
+
+}  // namespace
+
+struct tn_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::vector<NetRec> nets;
+  std::vector<InstRec> insts;
+  std::map<PlanKey, CachedPlan> plans;
+  double* arena = nullptr;
+  size_t arena_bytes = 0;
+  double* inbuf = nullptr;
+  size_t inbuf_bytes = 0;
+  // per-instance scratch
+  int scratch_batch = 0;
+  long long* expo = nullptr;
+  int* status = nullptr;
+  int* jac_ws = nullptr;
+  unsigned long long* maxbits = nullptr;
+  double* out_log = nullptr;
+  int* out_sign = nullptr;
+  // profiling
+  bool profile = false;
+  int64_t prof_launches[kNumFamily] = {0};
+  double prof_ms[kNumFamily] = {0};
+};
+
+namespace {
+
+int fail(tn_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(tn_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, TN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+cudaError_t ensure(T** p, size_t* have, size_t need) {
+  if (*have >= need && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), need);
+  if (e == cudaSuccess) *have = need;
+  return e;
+}
+
+int load_structure(tn_ctx* c, int32_t n_bonds, const int64_t* bond_dims, int32_t n_tensors,
+                   const int32_t* ndims, const int32_t* bond_ids, tnp::Structure* st) {
+  if (n_bonds < 0 || n_tensors < 1) return fail(c, TN_EINVAL, "network needs >= 1 tensor");
+  if (n_bonds > 0 && !bond_dims) return fail(c, TN_EINVAL, "bond_dims is NULL");
+  if (!ndims || (n_bonds > 0 && !bond_ids)) return fail(c, TN_EINVAL, "ndims / bond_ids is NULL");
+  st->bond_dims.assign(bond_dims, bond_dims + n_bonds);
+  for (int64_t d : st->bond_dims)
+    if (d < 1 || d > (1ll << 31)) return fail(c, TN_ESHAPE, "bond size out of range");
+  std::vector<int> count(n_bonds, 0), first(n_bonds, -1);
+  st->bonds.assign(n_tensors, {});
+  st->in_off.assign(n_tensors, 0);
+  int64_t pos = 0, off = 0;
+  for (int t = 0; t < n_tensors; ++t) {
+    if (ndims[t] < 0 || ndims[t] > tnk::kMaxDims)
+      return fail(c, TN_ESHAPE, "tensor " + std::to_string(t) + ": bad number of bonds");
+    double sz = 1.0;
+    int64_t isz = 1;
+    for (int a = 0; a < ndims[t]; ++a) {
+      int b = bond_ids[pos++];
+      if (b < 0 || b >= n_bonds)
+        return fail(c, TN_ESHAPE, "tensor " + std::to_string(t) + ": bond id out of range");
+      if (first[b] == t)
+        return fail(c, TN_ESHAPE, "tensor " + std::to_string(t) + " lists bond " + std::to_string(b) + " twice");
+      if (first[b] < 0) first[b] = t;
+      count[b]++;
+      st->bonds[t].push_back(b);
+      sz *= (double)st->bond_dims[b];
+      isz *= st->bond_dims[b];
+    }
+    if (sz > 4e9) return fail(c, TN_ESHAPE, "tensor " + std::to_string(t) + " too large");
+    st->in_off[t] = off;
+    off += (isz + 31) / 32 * 32;
+  }
+  for (int b = 0; b < n_bonds; ++b)
+    if (count[b] != 2)
+      return fail(c, TN_ESHAPE,
+                  "bond " + std::to_string(b) + " appears " + std::to_string(count[b]) + " times (need 2)");
+  st->in_total = off;
+  return TN_OK;
+}
+
+uint64_t structure_hash(const tnp::Structure& st) {
+  uint64_t h = 1469598103934665603ull;
+  size_t nb = st.bond_dims.size();
+  h = fnv(h, &nb, sizeof nb);
+  h = fnv(h, st.bond_dims.data(), nb * sizeof(int64_t));
+  for (auto& bl : st.bonds) {
+    size_t n = bl.size();
+    h = fnv(h, &n, sizeof n);
+    h = fnv(h, bl.data(), n * sizeof(int));
+  }
+  return h;
+}
+
+int add_network(tn_ctx* c, tnp::Structure&& st, const double* const* data, bool data_on_device,
+                const std::vector<double>* flat_host, int* net_id) {
+  NetRec rec;
+  rec.st = std::move(st);
+  rec.hash = structure_hash(rec.st);
+  const int nt = (int)rec.st.bonds.size();
+  // finiteness check on host data
+  auto tsize = [&](int t) {
+    int64_t s = 1;
+    for (int b : rec.st.bonds[t]) s *= rec.st.bond_dims[b];
+    return s;
+  };
+  if (!data_on_device) {
+    for (int t = 0; t < nt; ++t) {
+      const double* d = flat_host ? flat_host->data() + rec.st.in_off[t] : data[t];
+      if (!d) return fail(c, TN_EINVAL, "tensor data pointer is NULL");
+      int64_t s = tsize(t);
+      for (int64_t i = 0; i < s; ++i)
+        if (!std::isfinite(d[i]))
+          return fail(c, TN_ENONFINITE, "tensor " + std::to_string(t) + " has a non-finite entry");
+    }
+  }
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMalloc(&rec.d_data, sizeof(double) * std::max<int64_t>(rec.st.in_total, 1));
+  if (e != cudaSuccess) return fail(c, TN_ENOMEM, "cudaMalloc network data failed");
+  cudaMemsetAsync(rec.d_data, 0, sizeof(double) * std::max<int64_t>(rec.st.in_total, 1), c->stream);
+  if (flat_host) {
+    e = cudaMemcpyAsync(rec.d_data, flat_host->data(), sizeof(double) * rec.st.in_total,
+                        cudaMemcpyHostToDevice, c->stream);
+  } else {
+    for (int t = 0; t < nt && e == cudaSuccess; ++t)
+      e = cudaMemcpyAsync(rec.d_data + rec.st.in_off[t], data[t], sizeof(double) * tsize(t),
+                          data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(rec.d_data);
+    return cuda_fail(c, e, "copy network data");
+  }
+  c->nets.push_back(std::move(rec));
+  *net_id = (int)c->nets.size() - 1;
+  return TN_OK;
+}
+
+int add_tree(tn_ctx* c, int net_id, int32_t n_inputs, int32_t n_ops, const int32_t* ops, int* inst_id) {
+  if (net_id < 0 || net_id >= (int)c->nets.size()) return fail(c, TN_EINVAL, "unknown network id");
+  if (n_ops < 0 || (n_ops > 0 && !ops)) return fail(c, TN_EINVAL, "bad ops");
+  InstRec r;
+  r.net = net_id;
+  r.n_inputs = n_inputs;
+  r.ops.assign(ops, ops + 4 * (size_t)n_ops);
+  for (int32_t q = 0; q < n_ops; ++q)
+    if (r.ops[4 * q] == 1) r.ops[4 * q + 3] = -1;
+  std::string err = tnp::validate_tree(c->nets[net_id].st, r.ops, n_inputs);
+  if (!err.empty()) return fail(c, TN_EFORMAT, "tree: " + err);
+  uint64_t h = c->nets[net_id].hash;
+  h = fnv(h, &n_inputs, sizeof n_inputs);
+  h = fnv(h, r.ops.data(), r.ops.size() * sizeof(int32_t));
+  r.hash = h;
+  c->insts.push_back(std::move(r));
+  *inst_id = (int)c->insts.size() - 1;
+  return TN_OK;
+}
+
+bool same_group(const tn_ctx* c, int a, int b) {
+  const InstRec &x = c->insts[a], &y = c->insts[b];
+  if (x.hash != y.hash || x.ops != y.ops || x.n_inputs != y.n_inputs) return false;
+  const tnp::Structure &s = c->nets[x.net].st, &t = c->nets[y.net].st;
+  return s.bond_dims == t.bond_dims && s.bonds == t.bonds;
+}
+
+int ensure_scratch(tn_ctx* c, int batch) {
+  if (c->scratch_batch >= batch) return TN_OK;
+  cudaFree(c->expo);
+  cudaFree(c->status);
+  cudaFree(c->jac_ws);
+  cudaFree(c->maxbits);
+  cudaFree(c->out_log);
+  cudaFree(c->out_sign);
+  c->scratch_batch = 0;
+  if (cudaMalloc(&c->expo, sizeof(long long) * batch) != cudaSuccess ||
+      cudaMalloc(&c->status, sizeof(int) * batch) != cudaSuccess ||
+      cudaMalloc(&c->jac_ws, sizeof(int) * 64 * batch) != cudaSuccess ||
+      cudaMalloc(&c->maxbits, sizeof(unsigned long long) * batch) != cudaSuccess ||
+      cudaMalloc(&c->out_log, sizeof(double) * batch) != cudaSuccess ||
+      cudaMalloc(&c->out_sign, sizeof(int) * batch) != cudaSuccess)
+    return fail(c, TN_ENOMEM, "scratch allocation failed");
+  c->scratch_batch = batch;
+  return TN_OK;
+}
+
+const tnp::Plan* get_plan(tn_ctx* c, int inst, int chi, int prec, int* rc) {
+  PlanKey key{c->insts[inst].hash, chi, prec};
+  auto it = c->plans.find(key);
+  if (it != c->plans.end() && same_group(c, it->second.inst_proto, inst)) return &it->second.plan;
+  CachedPlan cp;
+  cp.inst_proto = inst;
+  const InstRec& r = c->insts[inst];
+  std::string err = tnp::build_plan(c->nets[r.net].st, r.ops, r.n_inputs, chi, prec, &cp.plan);
+  if (!err.empty()) {
+    *rc = fail(c, TN_EFORMAT, "plan: " + err);
+    return nullptr;
+  }
+  auto res = c->plans.insert_or_assign(key, std::move(cp));
+  return &res.first->second.plan;
+}
+
+// Run the plan on a batch.  With stop_op >= 0, only the steps of tree ops
+// 0..stop_op run (no final read-out) and the call returns after syncing; the
+// arena then holds every tensor alive after that op.
+int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members, double* logabs,
+              int* sign, int stop_op = -1) {
+  const int batch = (int)members.size();
+  if (batch > 65535) return fail(c, TN_EINVAL, "more than 65535 instances in one batch");
+  const tnp::Structure& st = c->nets[c->insts[members[0]].net].st;
+  cudaError_t e;
+  const size_t arena_need = sizeof(double) * (size_t)std::max<int64_t>(plan.arena_units, 1) * batch;
+  if ((e = ensure(&c->arena, &c->arena_bytes, arena_need)) != cudaSuccess)
+    return fail(c, TN_ENOMEM, "arena allocation of " + std::to_string(arena_need) + " bytes failed");
+  const size_t in_need = sizeof(double) * (size_t)std::max<int64_t>(st.in_total, 1) * batch;
+  if ((e = ensure(&c->inbuf, &c->inbuf_bytes, in_need)) != cudaSuccess)
+    return fail(c, TN_ENOMEM, "input buffer allocation failed");
+  int rc = ensure_scratch(c, batch);
+  if (rc != TN_OK) return rc;
+  cudaStream_t s = c->stream;
+  for (int b = 0; b < batch; ++b) {
+    const NetRec& nr = c->nets[c->insts[members[b]].net];
+    e = cudaMemcpyAsync(c->inbuf + (size_t)b * st.in_total, nr.d_data, sizeof(double) * st.in_total,
+                        cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "gather inputs");
+  }
+  cudaMemsetAsync(c->expo, 0, sizeof(long long) * batch, s);
+  cudaMemsetAsync(c->status, 0, sizeof(int) * batch, s);
+  tnk::DevState ds{c->expo, c->status};
+  auto ptr = [&](const tnp::PView& v) -> double* {
+    return v.buf == tnp::BUF_INPUT ? c->inbuf + v.off : c->arena + v.off * batch;
+  };
+  auto cview = [&](const tnp::PView& v) { return tnk::View{ptr(v), v.rs, v.cs, v.bs}; };
+  auto wview = [&](const tnp::PView& v) { return tnk::ViewW{ptr(v), v.rs, v.cs, v.bs}; };
+
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+  std::vector<int> ev_family;
+  for (const tnp::Step& stp : plan.steps) {
+    if (stop_op >= 0 && (stp.op_index > stop_op || stp.kind == tnp::ST_FINAL)) break;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profile) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+    }
+    switch (stp.kind) {
+      case tnp::ST_PERMUTE:
+        e = tnk::permute_f64(ptr(stp.src), stp.src.bs, ptr(stp.dst), stp.dst.bs, (int)stp.in_dims.size(),
+                             stp.in_dims.data(), stp.perm.data(), batch, s);
+        break;
+      case tnp::ST_GEMM:
+        e = tnk::gemm_f64(stp.m, stp.n, stp.k, stp.alpha, cview(stp.A), cview(stp.B), stp.beta, wview(stp.C),
+                          batch, s);
+        break;
+      case tnp::ST_QR:
+        e = tnk::qr_r_f64(stp.m, stp.n, cview(stp.A), ptr(stp.work), stp.work.bs, wview(stp.C), batch, s);
+        break;
+      case tnp::ST_JACOBI:
+        e = tnk::jacobi_svd_f64(stp.m, stp.n, ptr(stp.C), stp.C.bs, ptr(stp.aux1), stp.aux1.bs,
+                                ptr(stp.aux2), stp.aux2.bs, c->jac_ws, ds, stp.init_v, batch, s);
+        break;
+      case tnp::ST_TO_F32:
+        e = tnk::convert_f64_to_f32(ptr(stp.src), stp.count, stp.src.bs, reinterpret_cast<float*>(ptr(stp.dst)),
+                                    stp.fbs_dst, batch, s);
+        break;
+      case tnp::ST_JACOBI32:
+        e = tnk::jacobi_svd_f32(stp.m, stp.n, reinterpret_cast<float*>(ptr(stp.C)), stp.fbs_src,
+                                reinterpret_cast<float*>(ptr(stp.aux1)), stp.fbs_dst, c->jac_ws, ds, batch, s);
+        break;
+      case tnp::ST_COPY:
+        e = cudaMemcpyAsync(ptr(stp.dst), ptr(stp.src), sizeof(double) * (size_t)stp.dst.bs * batch,
+                            cudaMemcpyDeviceToDevice, s);
+        break;
+      case tnp::ST_TO_F64:
+        e = tnk::convert_f32_to_f64(reinterpret_cast<const float*>(ptr(stp.src)), stp.count, stp.fbs_src,
+                                    ptr(stp.dst), ptr(stp.out1), stp.dst.bs, batch, s);
+        break;
+      case tnp::ST_SELECT:
+        e = tnk::select_scale_f64(stp.m, stp.n, stp.k, ptr(stp.C), stp.C.bs, ptr(stp.aux1), stp.aux1.bs,
+                                  ptr(stp.aux2), stp.aux2.bs, ptr(stp.out1), stp.out1.bs, (int)stp.count,
+                                  ptr(stp.out2), stp.out2.bs, stp.init_v, batch, s);
+        break;
+      case tnp::ST_APPLYQ:
+        e = tnk::apply_q_f64(stp.m, stp.n, ptr(stp.work), stp.work.bs, ptr(stp.C), stp.C.bs, stp.k, batch, s);
+        break;
+      case tnp::ST_RESCALE:
+        e = tnk::rescale_f64(ptr(stp.C), stp.count, stp.C.bs, c->maxbits, ds, batch, s);
+        break;
+      case tnp::ST_FINAL:
+        e = tnk::finalize_f64(ptr(stp.C), stp.C.bs, ds, c->out_log, c->out_sign, batch, s);
+        break;
+      default:
+        e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) {
+      return fail(c, TN_ECUDA, std::string("launch of ") + kFamily[stp.kind] + " (tree op " +
+                                   std::to_string(stp.op_index) + ") failed: " + cudaGetErrorString(e));
+    }
+    if (c->profile) {
+      cudaEventRecord(e1, s);
+      evs.push_back({e0, e1});
+      ev_family.push_back(stp.kind);
+    }
+  }
+  if (stop_op >= 0) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "partial run");
+    return TN_OK;
+  }
+  std::vector<double> hl(batch);
+  std::vector<int> hs(batch), hst(batch);
+  e = cudaMemcpyAsync(hl.data(), c->out_log, sizeof(double) * batch, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), c->out_sign, sizeof(int) * batch, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), c->status, sizeof(int) * batch, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+  for (size_t q = 0; q < evs.size(); ++q) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, evs[q].first, evs[q].second);
+    c->prof_ms[ev_family[q]] += ms;
+    c->prof_launches[ev_family[q]] += 1;
+    cudaEventDestroy(evs[q].first);
+    cudaEventDestroy(evs[q].second);
+  }
+  int worst = 0;
+  for (int b = 0; b < batch; ++b) {
+    logabs[b] = hl[b];
+    sign[b] = hs[b];
+    if (hst[b] != 0 && worst == 0) worst = hst[b];
+  }
+  if (worst == -9) return fail(c, TN_ENOCONV, "Jacobi SVD did not converge");
+  if (worst == -7) return fail(c, TN_ENONFINITE, "non-finite intermediate");
+  if (worst != 0) return fail(c, TN_ECUDA, "device status " + std::to_string(worst));
+  return TN_OK;
+}
+
+bool read_file(const char* path, std::string* out) {
+  std::ifstream f(path, std::ios::binary);
+  if (!f) return false;
+  std::ostringstream ss;
+  ss << f.rdbuf();
+  *out = ss.str();
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tn_version(void) { return "tn-gb300 0.1"; }
+
+int tn_create(tn_ctx** out, int device) {
+  if (!out) return TN_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TN_ECUDA;
+  tn_ctx* c = new (std::nothrow) tn_ctx();
+  if (!c) return TN_ENOMEM;
+  c->device = device;
+  *out = c;
+  return TN_OK;
+}
+
+void tn_destroy(tn_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  for (auto& n : c->nets) cudaFree(n.d_data);
+  cudaFree(c->arena);
+  cudaFree(c->inbuf);
+  cudaFree(c->expo);
+  cudaFree(c->status);
+  cudaFree(c->jac_ws);
+  cudaFree(c->maxbits);
+  cudaFree(c->out_log);
+  cudaFree(c->out_sign);
+  delete c;
+}
+
+int tn_set_stream(tn_ctx* c, void* stream) {
+  if (!c) return TN_EINVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return TN_OK;
+}
+
+int tn_load_network(tn_ctx* c, const tn_network_desc* d, int* net_id) {
+  if (!c || !d || !net_id) return fail(c, TN_EINVAL, "NULL argument");
+  if (!d->data) return fail(c, TN_EINVAL, "data is NULL");
+  tnp::Structure st;
+  int rc = load_structure(c, d->n_bonds, d->bond_dims, d->n_tensors, d->ndims, d->bond_ids, &st);
+  if (rc != TN_OK) return rc;
+  return add_network(c, std::move(st), d->data, false, nullptr, net_id);
+}
+
+int tn_load_network_file(tn_ctx* c, const char* path, int* net_id) {
+  if (!c || !path || !net_id) return fail(c, TN_EINVAL, "NULL argument");
+  std::string buf;
+  if (!read_file(path, &buf)) return fail(c, TN_EINVAL, std::string("cannot read ") + path);
+  size_t off = 0;
+  auto need = [&](size_t n) { return off + n <= buf.size(); };
+  auto rd64 = [&](int64_t* v) {
+    if (!need(8)) return false;
+    std::memcpy(v, buf.data() + off, 8);
+    off += 8;
+    return true;
+  };
+  if (!need(8) || std::memcmp(buf.data(), "TNNET1\0\0", 8) != 0) return fail(c, TN_EFORMAT, "not a TNNET1 file");
+  off = 8;
+  int64_t nb, nt;
+  if (!rd64(&nb) || !rd64(&nt) || nb < 0 || nt < 1 || nb > (1 << 28) || nt > (1 << 28))
+    return fail(c, TN_EFORMAT, "bad header");
+  std::vector<int64_t> dims(nb);
+  for (auto& d : dims)
+    if (!rd64(&d)) return fail(c, TN_EFORMAT, "truncated bond sizes");
+  std::vector<int32_t> ndims(nt), ids;
+  for (int64_t t = 0; t < nt; ++t) {
+    int64_t nd;
+    if (!rd64(&nd) || nd < 0 || nd > tnk::kMaxDims) return fail(c, TN_EFORMAT, "bad tensor header");
+    ndims[t] = (int32_t)nd;
+    for (int64_t a = 0; a < nd; ++a) {
+      int64_t b;
+      if (!rd64(&b) || b < 0 || b >= nb) return fail(c, TN_EFORMAT, "bad bond id");
+      ids.push_back((int32_t)b);
+    }
+  }
+  tnp::Structure st;
+  int rc = load_structure(c, (int32_t)nb, dims.data(), (int32_t)nt, ndims.data(), ids.data(), &st);
+  if (rc != TN_OK) return rc;
+  std::vector<double> flat((size_t)std::max<int64_t>(st.in_total, 1), 0.0);
+  for (int64_t t = 0; t < nt; ++t) {
+    int64_t s = 1;
+    for (int b : st.bonds[t]) s *= st.bond_dims[b];
+    if (!need(8 * (size_t)s)) return fail(c, TN_EFORMAT, "truncated tensor data");
+    std::memcpy(flat.data() + st.in_off[t], buf.data() + off, 8 * (size_t)s);
+    off += 8 * (size_t)s;
+  }
+  return add_network(c, std::move(st), nullptr, false, &flat, net_id);
+}
+
+int tn_set_network_data(tn_ctx* c, int net_id, const double* const* data, int on_device) {
+  if (!c || !data) return fail(c, TN_EINVAL, "NULL argument");
+  if (net_id < 0 || net_id >= (int)c->nets.size()) return fail(c, TN_EINVAL, "unknown network id");
+  NetRec& nr = c->nets[net_id];
+  DeviceGuard g(c->device);
+  for (size_t t = 0; t < nr.st.bonds.size(); ++t) {
+    int64_t s = 1;
+    for (int b : nr.st.bonds[t]) s *= nr.st.bond_dims[b];
+    if (!data[t]) return fail(c, TN_EINVAL, "tensor data pointer is NULL");
+    if (!on_device)
+      for (int64_t i = 0; i < s; ++i)
+        if (!std::isfinite(data[t][i]))
+          return fail(c, TN_ENONFINITE, "tensor " + std::to_string(t) + " has a non-finite entry");
+    cudaError_t e = cudaMemcpyAsync(nr.d_data + nr.st.in_off[t], data[t], sizeof(double) * s,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set network data");
+  }
+  return TN_OK;
+}
+
+int tn_load_tree(tn_ctx* c, int net_id, const tn_tree_desc* d, int* inst_id) {
+  if (!c || !d || !inst_id) return fail(c, TN_EINVAL, "NULL argument");
+  return add_tree(c, net_id, d->n_inputs, d->n_ops, d->ops, inst_id);
+}
+
+int tn_load_tree_file(tn_ctx* c, int net_id, const char* path, int* inst_id) {
+  if (!c || !path || !inst_id) return fail(c, TN_EINVAL, "NULL argument");
+  std::string buf;
+  if (!read_file(path, &buf)) return fail(c, TN_EINVAL, std::string("cannot read ") + path);
+  std::istringstream in(buf);
+  std::string line;
+  int n_inputs = -1, ln = 0;
+  std::vector<int32_t> ops;
+  while (std::getline(in, line)) {
+    ++ln;
+    size_t h = line.find('#');
+    if (h != std::string::npos) line.resize(h);
+    std::istringstream ls(line);
+    std::string tok;
+    if (!(ls >> tok)) continue;
+    if (tok == "tntree") continue;
+    if (tok == "inputs") {
+      if (!(ls >> n_inputs)) return fail(c, TN_EFORMAT, "tree line " + std::to_string(ln) + ": bad inputs");
+    } else if (tok == "C") {
+      int i, j, k;
+      if (!(ls >> i >> j >> k)) return fail(c, TN_EFORMAT, "tree line " + std::to_string(ln) + ": bad C op");
+      ops.insert(ops.end(), {0, i, j, k});
+    } else if (tok == "S") {
+      int i, j;
+      if (!(ls >> i >> j)) return fail(c, TN_EFORMAT, "tree line " + std::to_string(ln) + ": bad S op");
+      ops.insert(ops.end(), {1, i, j, -1});
+    } else {
+      return fail(c, TN_EFORMAT, "tree line " + std::to_string(ln) + ": unknown token " + tok);
+    }
+  }
+  if (n_inputs < 0) return fail(c, TN_EFORMAT, "tree file has no inputs line");
+  return add_tree(c, net_id, n_inputs, (int32_t)(ops.size() / 4), ops.data(), inst_id);
+}
+
+int tn_contract_approx(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, double* logabsz_out,
+                       int* sign_out) {
+  if (!c || !inst_ids || !logabsz_out || !sign_out || n_inst < 1) return fail(c, TN_EINVAL, "bad arguments");
+  if (chi < 1) return fail(c, TN_EINVAL, "chi must be >= 1");
+  if (prec != TN_F64) return fail(c, TN_EINVAL, "precision form not available in this build");
+  for (int q = 0; q < n_inst; ++q)
+    if (inst_ids[q] < 0 || inst_ids[q] >= (int)c->insts.size()) return fail(c, TN_EINVAL, "unknown instance id");
+  DeviceGuard g(c->device);
+  std::vector<bool> done(n_inst, false);
+  for (int q = 0; q < n_inst; ++q) {
+    if (done[q]) continue;
+    std::vector<int> members, pos;
+    for (int r = q; r < n_inst; ++r)
+      if (!done[r] && same_group(c, inst_ids[q], inst_ids[r])) {
+        members.push_back(inst_ids[r]);
+        pos.push_back(r);
+        done[r] = true;
+      }
+    int rc = TN_OK;
+    const tnp::Plan* plan = get_plan(c, inst_ids[q], chi, prec, &rc);
+    if (!plan) return rc;
+    std::vector<double> lg(members.size());
+    std::vector<int> sg(members.size());
+    rc = run_group(c, *plan, members, lg.data(), sg.data());
+    if (rc != TN_OK) return rc;
+    for (size_t m = 0; m < members.size(); ++m) {
+      logabsz_out[pos[m]] = lg[m];
+      sign_out[pos[m]] = sg[m];
+    }
+  }
+  return TN_OK;
+}
+
+int tn_debug_tensor(tn_ctx* c, int n_inst, const int* inst_ids, int which, int chi, int prec, int stop_op,
+                    int tensor_id, double* out, int64_t cap, int32_t* ndim_out, int32_t* bond_ids_out,
+                    int64_t* dims_out) {
+  if (!c || !inst_ids || !ndim_out || n_inst < 1 || which < 0 || which >= n_inst)
+    return fail(c, TN_EINVAL, "bad arguments");
+  if (chi < 1) return fail(c, TN_EINVAL, "chi must be >= 1");
+  if (prec != TN_F64) return fail(c, TN_EINVAL, "precision form not available in this build");
+  for (int q = 0; q < n_inst; ++q) {
+    if (inst_ids[q] < 0 || inst_ids[q] >= (int)c->insts.size()) return fail(c, TN_EINVAL, "unknown instance id");
+    if (!same_group(c, inst_ids[0], inst_ids[q])) return fail(c, TN_EINVAL, "instances do not share a tree and structure");
+  }
+  DeviceGuard g(c->device);
+  int rc = TN_OK;
+  const tnp::Plan* plan = get_plan(c, inst_ids[0], chi, prec, &rc);
+  if (!plan) return rc;
+  const tnp::TensorRec* rec = nullptr;
+  for (const auto& r : plan->records)
+    if (r.tensor_id == tensor_id && r.op_index <= stop_op) rec = &r;
+  if (!rec) return fail(c, TN_EINVAL, "tensor does not exist after that op");
+  for (const auto& cs : plan->consumed)
+    if (cs.second == tensor_id && cs.first > rec->op_index && cs.first <= stop_op)
+      return fail(c, TN_EINVAL, "tensor was contracted away before that op");
+  int64_t size = 1;
+  for (int64_t d : rec->dims) size *= d;
+  *ndim_out = (int32_t)rec->bonds.size();
+  if (bond_ids_out)
+    for (size_t a = 0; a < rec->bonds.size() && a < (size_t)tnk::kMaxDims; ++a) bond_ids_out[a] = rec->bonds[a];
+  if (dims_out)
+    for (size_t a = 0; a < rec->dims.size() && a < (size_t)tnk::kMaxDims; ++a) dims_out[a] = rec->dims[a];
+  if (!out) return TN_OK;  // shape query only
+  if (cap < size) return fail(c, TN_EINVAL, "output buffer too small");
+  std::vector<int> members(inst_ids, inst_ids + n_inst);
+  std::vector<double> lg(n_inst);
+  std::vector<int> sg(n_inst);
+  rc = run_group(c, *plan, members, lg.data(), sg.data(), stop_op < 0 ? INT32_MAX : stop_op);
+  if (rc != TN_OK) return rc;
+  const int batch = n_inst;
+  const double* base = rec->view.buf == tnp::BUF_INPUT ? c->inbuf + rec->view.off : c->arena + rec->view.off * batch;
+  cudaError_t e = cudaMemcpy(out, base + (int64_t)which * rec->view.bs, sizeof(double) * size, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fetch tensor");
+  return TN_OK;
+}
+
+int tn_plan_stats_get(tn_ctx* c, int inst_id, int chi, int prec, tn_plan_stats* out) {
+  if (!c || !out) return fail(c, TN_EINVAL, "NULL argument");
+  if (inst_id < 0 || inst_id >= (int)c->insts.size()) return fail(c, TN_EINVAL, "unknown instance id");
+  if (chi < 1) return fail(c, TN_EINVAL, "chi must be >= 1");
+  int rc = TN_OK;
+  const tnp::Plan* p = get_plan(c, inst_id, chi, prec, &rc);
+  if (!p) return rc;
+  out->n_contractions = p->n_contractions;
+  out->n_compressions = p->n_compressions;
+  out->gemm_flops = p->gemm_flops;
+  out->qr_flops = p->qr_flops;
+  out->svd_flops = p->svd_flops;
+  out->permute_bytes = p->permute_bytes;
+  out->peak_bytes = 8.0 * (double)p->arena_units;
+  int64_t launches = 0;
+  for (auto& s : p->steps)  // rescale = max + scale kernels; copies are not kernels
+    launches += (s.kind == tnp::ST_RESCALE) ? 2 : (s.kind == tnp::ST_COPY ? 0 : 1);
+  out->kernel_launches = launches;
+  return TN_OK;
+}
+
+int tn_profile_enable(tn_ctx* c, int enable) {
+  if (!c) return TN_EINVAL;
+  c->profile = enable != 0;
+  for (int f = 0; f < kNumFamily; ++f) {
+    c->prof_launches[f] = 0;
+    c->prof_ms[f] = 0.0;
+  }
+  return TN_OK;
+}
+
+int tn_kernel_times(tn_ctx* c, int cap, const char** names, int64_t* launches, double* total_ms) {
+  if (!c) return TN_EINVAL;
+  int n = 0;
+  for (int f = 0; f < kNumFamily; ++f) {
+    if (c->prof_launches[f] == 0) continue;
+    if (n < cap) {
+      if (names) names[n] = kFamily[f];
+      if (launches) launches[n] = c->prof_launches[f];
+      if (total_ms) total_ms[n] = c->prof_ms[f];
+    }
+    ++n;
+  }
+  return n;
+}
+
+const char* tn_last_error(const tn_ctx* c) {
+  if (!c) return "NULL context";
+  return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal launchers of the CUDA kernels (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace tnk {
+
+constexpr int kMaxDims = 24;
+
+// A batched strided 2-D view: element (r, c) of batch b at p[b*bs + r*rs + c*cs].
+struct View {
+  const double* p;
+  int64_t rs, cs, bs;
+};
+struct ViewW {
+  double* p;
+  int64_t rs, cs, bs;
+};
+
+// Per-instance bookkeeping on the device.
+struct DevState {
+  long long* expo;   // [batch] running power-of-two exponent E
+  int* status;       // [batch] 0 = ok, else a tn_status-like code set by a kernel
+};
+
+// out[b] = in[b] with axes permuted: output axis a is input axis perm[a].
+// in_dims are the input's axis sizes (row-major).  Bandwidth-bound.
+cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t out_bs, int nd,
+                        const int64_t* in_dims, const int* perm, int batch, cudaStream_t s);
+
+// C[b] = alpha * A[b] (m x k) * B[b] (k x n) + beta * C[b], FP64 on the CUDA cores
+// (beta == 0 never reads C).
+cudaError_t gemm_f64(int m, int n, int k, double alpha, View A, View B, double beta, ViewW C,
+                     int batch, cudaStream_t s);
+
+// Householder QR of A[b] (m x n, any strides): R factor out, reflectors kept.
+// work: column-major m x n scratch per batch (stride work_bs >= m*n), followed
+// by batch * n doubles of tau; on return it holds the reflectors for
+// apply_q_f64.  R: row-major r x n output (r = min(m, n)), zero below the diagonal.
+cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW R, int batch,
+                     cudaStream_t s);
+
+// One-sided Jacobi SVD of G[b] (m x n column-major, m >= n, leading dim m):
+// on return G holds G V (columns sigma_i u_i) and V (n x n column-major) the
+// accumulated rotations (V = I first when init_v), sig the FP64 column norms
+// sigma_i (unsorted).  ws: 64 ints per batch of scratch.  Sets st.status[b] = -9
+// if the bounded sweep loop ran out.
+cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int64_t v_bs,
+                           double* sig, int64_t sig_bs, int* ws, DevState st, int init_v,
+                           int batch, cudaStream_t s);
+// The FP32 preconditioning pass (V = I first); never sets a status.
+cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64_t v_bs, int* ws,
+                           DevState st, int batch, cudaStream_t s);
+// y = (float) x and y1 (= y2 when given) = (double) x, n elements per batch.
+cudaError_t convert_f64_to_f32(const double* x, int64_t n, int64_t xbs, float* y, int64_t ybs,
+                               int batch, cudaStream_t s);
+cudaError_t convert_f32_to_f64(const float* x, int64_t n, int64_t xbs, double* y1, double* y2,
+                               int64_t ybs, int batch, cudaStream_t s);
+
+// After Jacobi: pick the k largest sigma and write the truncated factors
+// with sigma^1/2 absorbed: L[:, p] = g_i / sqrt(sigma_i) (= u_i sqrt(sigma_i)),
+// R[:, p] = V[:, i] sqrt(sigma_i); column-major with leading dims ldl >= m,
+// ldr >= n, rows beyond m (n) zero-filled.
+cudaError_t select_scale_f64(int m, int n, int k, const double* G, int64_t g_bs, const double* V,
+                             int64_t v_bs, const double* sig, int64_t sig_bs, double* L, int64_t l_bs,
+                             int ldl, double* R, int64_t r_bs, int ldr, int batch, cudaStream_t s);
+
+// X[b] <- Q[b] X[b], Q the Householder product a qr_r_f64 call left in `work`
+// (same m, n, work, work_bs and batch).  X: m x k column-major (ld m).
+cudaError_t apply_q_f64(int m, int n, const double* work, int64_t work_bs, double* X, int64_t x_bs, int k,
+                        int batch, cudaStream_t s);
+
+// X[b] *= 2^-e_b with e_b the binary exponent of max|X[b]|; st.expo[b] += e_b.
+// maxbits: [batch] device scratch.
+cudaError_t rescale_f64(double* X, int64_t n, int64_t bs, unsigned long long* maxbits, DevState st,
+                        int batch, cudaStream_t s);
+
+// Final: out_log[b] = ln|x[b]| + expo[b] ln 2 (device arrays), out_sign[b].
+cudaError_t finalize_f64(const double* x, int64_t bs, DevState st, double* out_log, int* out_sign,
+                         int batch, cudaStream_t s);
+
+// Fill a batch of n x n column-major matrices with the identity.
+cudaError_t set_identity_f64(double* V, int n, int64_t bs, int batch, cudaStream_t s);
+
+}  // namespace tnk

@@ -1,0 +1,589 @@
+// Schedule expansion: tree file + network structure + chi -> static steps.
+//
+// Semantics (Algorithm 1 with explicit ops; Sec. "Bond compression strategies"):
+//   C i j k  contracts all bonds shared by i and j; k's bonds are i's remaining
+//            bonds then j's remaining bonds.
+//   S i j    runs iff D_AB = prod(shared sizes) > chi; the shared bonds become one
+//            bond of size k = min(chi, D_A, D_B).
+// Physical layouts of intermediates are free (log Z does not depend on them),
+// so the planner tracks each tensor's storage order and hands row- or
+// column-major views to the GEMM / QR kernels instead of permuting; a permute
+// is issued only when the shared bonds are not contiguous at one end.
+//
+// A compression follows Eq. "svd" in its Q-form: R_A from a Householder QR
+// of A and L_B from one of B^T, the SVD R_A L_B = U s V^T, then
+// A_bar = Q_A U_k s^1/2 and B_bar = s^1/2 V_k^T Q_B with the Householder
+// products applied to the zero-padded factors (Q is never formed).  The
+// projector form of the SI (A P_L with P_L = L_B V_k s^-1/2) is the same
+// matrix in exact arithmetic but multiplies rounding by |A||B|/|AB|, which is
+// large when the entries cancel.  When D_A <= D_AB the QR of A is skipped
+// (R_A = A, i.e. Q_A = 1); likewise for B.
+#include "tn_plan.h"
+
+#include <algorithm>
+#include <map>
+#include <unordered_map>
+#include <unordered_set>
+
+namespace tnp {
+namespace {
+
+constexpr int64_t kAlign = 32;  // doubles: keeps every per-instance block 256-byte aligned
+
+int64_t round_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+class Arena {
+ public:
+  int64_t alloc(int64_t size) {
+    size = round_up(std::max<int64_t>(size, 1));
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= size) {
+        int64_t off = it->first, rest = it->second - size;
+        free_.erase(it);
+        if (rest) free_[off + size] = rest;
+        return off;
+      }
+    }
+    int64_t off = top_;
+    top_ += size;
+    peak_ = std::max(peak_, top_);
+    return off;
+  }
+  void release(int64_t off, int64_t size) {
+    size = round_up(std::max<int64_t>(size, 1));
+    auto it = free_.emplace(off, size).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+        it = pv;
+      }
+    }
+    if (it->first + it->second == top_) {
+      top_ = it->first;
+      free_.erase(it);
+    }
+  }
+  int64_t peak() const { return peak_; }
+
+ private:
+  std::map<int64_t, int64_t> free_;
+  int64_t top_ = 0, peak_ = 0;
+};
+
+struct Value {
+  std::vector<int> bonds;   // storage order
+  int64_t size = 1;
+  int buf = BUF_ARENA;
+  int64_t off = 0;
+  int64_t bs = 0;
+};
+
+int64_t prod_dims(const std::vector<int>& bl, const std::vector<int64_t>& dim) {
+  int64_t p = 1;
+  for (int b : bl) p *= dim[b];
+  return p;
+}
+
+// 0: bonds == X + Y; 1: bonds == Y + X; -1: neither.
+int layout_of(const std::vector<int>& bonds, const std::vector<int>& X, const std::vector<int>& Y) {
+  if (bonds.size() != X.size() + Y.size()) return -1;
+  bool xy = std::equal(X.begin(), X.end(), bonds.begin()) &&
+            std::equal(Y.begin(), Y.end(), bonds.begin() + X.size());
+  if (xy) return 0;
+  bool yx = std::equal(Y.begin(), Y.end(), bonds.begin()) &&
+            std::equal(X.begin(), X.end(), bonds.begin() + Y.size());
+  return yx ? 1 : -1;
+}
+
+double qr_flops(double m, double n) {
+  double M = std::max(m, n), r = std::min(m, n);
+  return 2.0 * M * r * r - 2.0 / 3.0 * r * r * r;
+}
+double svd_flops(double m, double n) {
+  double M = std::max(m, n), r = std::min(m, n);
+  return 4.0 * M * r * r - 4.0 / 3.0 * r * r * r;
+}
+
+struct Builder {
+  const Structure& s;
+  int chi;
+  Plan* plan;
+  Arena arena;
+  std::vector<Value> vals;
+  std::unordered_map<int, int> cur;  // tensor id -> value index
+  std::vector<int64_t> dim;          // bond sizes (grows with new bonds)
+  int op_index = -1;
+
+  PView base_view(const Value& v) const {
+    PView p;
+    p.buf = v.buf;
+    p.off = v.off;
+    p.bs = v.bs;
+    return p;
+  }
+  int new_arena_value(std::vector<int> bonds) {
+    Value v;
+    v.bonds = std::move(bonds);
+    v.size = prod_dims(v.bonds, dim);
+    v.buf = BUF_ARENA;
+    v.off = arena.alloc(v.size);
+    v.bs = round_up(std::max<int64_t>(v.size, 1));
+    vals.push_back(v);
+    return (int)vals.size() - 1;
+  }
+  PView temp(int64_t size, int64_t* off_out) {
+    PView p;
+    p.buf = BUF_ARENA;
+    p.off = arena.alloc(size);
+    p.bs = round_up(std::max<int64_t>(size, 1));
+    *off_out = p.off;
+    return p;
+  }
+  void record(int tensor_id, int vi) {
+    TensorRec r;
+    r.op_index = op_index;
+    r.tensor_id = tensor_id;
+    r.view = base_view(vals[vi]);
+    r.bonds = vals[vi].bonds;
+    for (int b : r.bonds) r.dims.push_back(dim[b]);
+    plan->records.push_back(std::move(r));
+  }
+  void release_value(int vi) {
+    Value& v = vals[vi];
+    if (v.buf == BUF_ARENA) arena.release(v.off, v.size);
+  }
+  void add(Step st) {
+    st.op_index = op_index;
+    plan->steps.push_back(std::move(st));
+  }
+  // permute value v into a new arena value whose storage order is `order`
+  int permute_to(int vi, const std::vector<int>& order) {
+    const Value src = vals[vi];
+    int out = new_arena_value(order);
+    Step st;
+    st.kind = ST_PERMUTE;
+    st.src = base_view(src);
+    st.dst = base_view(vals[out]);
+    for (int b : src.bonds) st.in_dims.push_back(dim[b]);
+    for (int b : order)
+      st.perm.push_back((int)(std::find(src.bonds.begin(), src.bonds.end(), b) - src.bonds.begin()));
+    st.count = src.size;
+    st.bytes = 16.0 * (double)src.size;
+    plan->permute_bytes += st.bytes;
+    add(st);
+    return out;
+  }
+  // overhead: a GEMM of the SVD's preconditioning (not counted as algorithmic work)
+  void gemm(int m, int n, int k, PView A, PView B, PView C, double alpha = 1.0, double beta = 0.0,
+            bool overhead = false) {
+    Step st;
+    st.kind = ST_GEMM;
+    st.m = m;
+    st.n = n;
+    st.k = k;
+    st.A = A;
+    st.B = B;
+    st.C = C;
+    st.alpha = alpha;
+    st.beta = beta;
+    st.flops = overhead ? 0.0 : 2.0 * m * n * (double)k;
+    st.bytes = 8.0 * ((double)m * k + (double)k * n + (double)m * n);
+    plan->gemm_flops += st.flops;
+    add(st);
+  }
+  void rescale(int vi) {
+    Step st;
+    st.kind = ST_RESCALE;
+    st.C = base_view(vals[vi]);
+    st.count = vals[vi].size;
+    st.bytes = 24.0 * (double)vals[vi].size;
+    add(st);
+  }
+
+  // Shared bonds in the order of `order_src`, plus the remaining bonds of each side.
+  struct Split {
+    std::vector<int> sh_i, sh_j, rem_i, rem_j;
+  };
+  Split split(const Value& a, const Value& b) const {
+    Split sp;
+    std::unordered_set<int> sb(b.bonds.begin(), b.bonds.end()), sa(a.bonds.begin(), a.bonds.end());
+    for (int x : a.bonds) (sb.count(x) ? sp.sh_i : sp.rem_i).push_back(x);
+    for (int x : b.bonds) (sa.count(x) ? sp.sh_j : sp.rem_j).push_back(x);
+    return sp;
+  }
+  // Choose the shared-bond order and permute operands only when needed.
+  // Returns (la, lb) layouts after any permutes; updates ia/ib to the values used.
+  void orient(int& ia, int& ib, const Split& sp, std::vector<int>& s_out, int& la, int& lb,
+              std::vector<int>& tmps) {
+    const std::vector<int>* cand[2] = {&sp.sh_i, &sp.sh_j};
+    int best = -1;
+    double best_cost = 1e300;
+    for (int c = 0; c < 2; ++c) {
+      const std::vector<int>& sv = *cand[c];
+      int a = layout_of(vals[ia].bonds, sp.rem_i, sv);
+      int b = layout_of(vals[ib].bonds, sv, sp.rem_j);
+      double cost = (a < 0 ? (double)vals[ia].size : 0.0) + (b < 0 ? (double)vals[ib].size : 0.0);
+      if (cost < best_cost) {
+        best_cost = cost;
+        best = c;
+      }
+    }
+    s_out = *cand[best];
+    la = layout_of(vals[ia].bonds, sp.rem_i, s_out);
+    lb = layout_of(vals[ib].bonds, s_out, sp.rem_j);
+    if (la < 0) {
+      std::vector<int> order = sp.rem_i;
+      order.insert(order.end(), s_out.begin(), s_out.end());
+      ia = permute_to(ia, order);
+      tmps.push_back(ia);
+      la = 0;
+    }
+    if (lb < 0) {
+      std::vector<int> order = s_out;
+      order.insert(order.end(), sp.rem_j.begin(), sp.rem_j.end());
+      ib = permute_to(ib, order);
+      tmps.push_back(ib);
+      lb = 0;
+    }
+  }
+
+  std::string contract(int i, int j, int k) {
+    int ia = cur.at(i), ib = cur.at(j);
+    const int ia0 = ia, ib0 = ib;
+    Split sp = split(vals[ia], vals[ib]);
+    std::vector<int> sh;
+    int la, lb;
+    std::vector<int> tmps;
+    orient(ia, ib, sp, sh, la, lb, tmps);
+    const int64_t m = prod_dims(sp.rem_i, dim), n = prod_dims(sp.rem_j, dim), kk = prod_dims(sh, dim);
+    if (m > INT32_MAX || n > INT32_MAX || kk > INT32_MAX) return "contraction too large";
+    PView A = base_view(vals[ia]);
+    if (la == 0) { A.rs = kk; A.cs = 1; } else { A.rs = 1; A.cs = m; }
+    PView B = base_view(vals[ib]);
+    if (lb == 0) { B.rs = n; B.cs = 1; } else { B.rs = 1; B.cs = kk; }
+    std::vector<int> nb = sp.rem_i;
+    nb.insert(nb.end(), sp.rem_j.begin(), sp.rem_j.end());
+    int ic = new_arena_value(nb);
+    PView C = base_view(vals[ic]);
+    C.rs = n;
+    C.cs = 1;
+    gemm((int)m, (int)n, (int)kk, A, B, C);
+    rescale(ic);
+    for (int t : tmps) release_value(t);
+    release_value(ia0);
+    release_value(ib0);
+    cur.erase(i);
+    cur.erase(j);
+    cur[k] = ic;
+    record(k, ic);
+    plan->consumed.push_back({op_index, i});
+    plan->consumed.push_back({op_index, j});
+    plan->n_contractions++;
+    return "";
+  }
+
+  std::string compress(int i, int j) {
+    int ia = cur.at(i), ib = cur.at(j);
+    const int ia0 = ia, ib0 = ib;
+    Split sp = split(vals[ia], vals[ib]);
+    const int64_t dab = prod_dims(sp.sh_i, dim);
+    if (dab <= chi) return "";
+    std::vector<int> sh;
+    int la, lb;
+    std::vector<int> tmps;
+    orient(ia, ib, sp, sh, la, lb, tmps);
+    const int64_t DA = prod_dims(sp.rem_i, dim), DB = prod_dims(sp.rem_j, dim);
+    if (DA > INT32_MAX || DB > INT32_MAX || dab > INT32_MAX) return "compression too large";
+    const int64_t rA = std::min(DA, dab), rB = std::min(DB, dab);
+    const int64_t kk = std::min<int64_t>(chi, std::min(rA, rB));
+    std::vector<std::pair<int64_t, int64_t>> trel;  // temporaries (off, size)
+    auto tmp = [&](int64_t size) {
+      int64_t off;
+      PView p = temp(size, &off);
+      trel.push_back({off, size});
+      return p;
+    };
+    PView A = base_view(vals[ia]);
+    if (la == 0) { A.rs = dab; A.cs = 1; } else { A.rs = 1; A.cs = DA; }
+    PView B = base_view(vals[ib]);
+    if (lb == 0) { B.rs = DB; B.cs = 1; } else { B.rs = 1; B.cs = dab; }
+    // R_A (rA x dab)
+    PView RA, workA, workB;
+    if (DA > dab) {
+      PView work = tmp(DA * dab + dab);
+      workA = work;
+      workA.bs = DA * dab;
+      RA = tmp(rA * dab);
+      RA.rs = dab;
+      RA.cs = 1;
+      Step st;
+      st.kind = ST_QR;
+      st.m = (int)DA;
+      st.n = (int)dab;
+      st.A = A;
+      st.work = work;
+      st.work.bs = DA * dab;
+      st.C = RA;
+      st.flops = qr_flops((double)DA, (double)dab);
+      st.bytes = 8.0 * (2.0 * DA * dab + (double)rA * dab);
+      plan->qr_flops += st.flops;
+      add(st);
+    } else {
+      RA = A;
+    }
+    // L_B (dab x rB) as the transpose of R of B^T (rB x dab)
+    PView LB;
+    if (DB > dab) {
+      PView work = tmp(DB * dab + dab);
+      workB = work;
+      workB.bs = DB * dab;
+      PView RBt = tmp(rB * dab);
+      RBt.rs = dab;
+      RBt.cs = 1;
+      PView Bt = B;
+      std::swap(Bt.rs, Bt.cs);
+      Step st;
+      st.kind = ST_QR;
+      st.m = (int)DB;
+      st.n = (int)dab;
+      st.A = Bt;
+      st.work = work;
+      st.work.bs = DB * dab;
+      st.C = RBt;
+      st.flops = qr_flops((double)DB, (double)dab);
+      st.bytes = 8.0 * (2.0 * DB * dab + (double)rB * dab);
+      plan->qr_flops += st.flops;
+      add(st);
+      LB = RBt;
+      std::swap(LB.rs, LB.cs);
+    } else {
+      LB = B;
+    }
+    // core M = R_A L_B, stored so that Jacobi sees an (Jm x Jn) column-major matrix, Jm >= Jn
+    // (M itself when rA >= rB, else M^T, i.e. M row-major)
+    const bool tall = rA >= rB;
+    const int64_t Jm = tall ? rA : rB, Jn = tall ? rB : rA;
+    PView M0 = tmp(rA * rB);
+    if (tall) { M0.rs = 1; M0.cs = rA; } else { M0.rs = rB; M0.cs = 1; }
+    gemm((int)rA, (int)rB, (int)dab, RA, LB, M0);
+    PView M0c = M0;  // the same buffer as a Jm x Jn column-major view
+    M0c.rs = 1;
+    M0c.cs = Jm;
+    // 1. FP32 preconditioner: Jacobi on a float copy from V = I
+    PView G32 = tmp((Jm * Jn + 1) / 2), V32 = tmp((Jn * Jn + 1) / 2);
+    {
+      Step st;
+      st.kind = ST_TO_F32;
+      st.src = M0;
+      st.dst = G32;
+      st.count = Jm * Jn;
+      st.fbs_dst = 2 * G32.bs;
+      st.bytes = 12.0 * (double)st.count;
+      add(st);
+      Step j;
+      j.kind = ST_JACOBI32;
+      j.m = (int)Jm;
+      j.n = (int)Jn;
+      j.C = G32;
+      j.aux1 = V32;
+      j.fbs_src = 2 * G32.bs;
+      j.fbs_dst = 2 * V32.bs;
+      add(j);
+    }
+    // 2. V <- two Newton-Schulz steps on the FP64 copy: V (1.5 I - 0.5 V^T V); G = M V
+    PView Vd = tmp(Jn * Jn), V = tmp(Jn * Jn), E = tmp(Jn * Jn);
+    {
+      Step st;
+      st.kind = ST_TO_F64;
+      st.src = V32;
+      st.dst = Vd;
+      st.out1 = V;
+      st.count = Jn * Jn;
+      st.fbs_src = 2 * V32.bs;
+      st.bytes = 20.0 * (double)st.count;
+      add(st);
+    }
+    PView VdT = Vd, VdN = Vd, Ec = E, Vc = V;
+    VdT.rs = Jn; VdT.cs = 1;
+    VdN.rs = 1; VdN.cs = Jn;
+    Ec.rs = Jn; Ec.cs = 1;
+    Vc.rs = 1; Vc.cs = Jn;
+    // step 1: E = Vd^T Vd, V = 1.5 V - 0.5 Vd E (V == Vd on entry)
+    gemm((int)Jn, (int)Jn, (int)Jn, VdT, VdN, Ec, 1.0, 0.0, /*overhead=*/true);
+    gemm((int)Jn, (int)Jn, (int)Jn, VdN, Ec, Vc, -0.5, 1.5, true);
+    // step 2: Vd = V, E = V^T V, V = 1.5 V - 0.5 Vd E
+    {
+      Step cp;
+      cp.kind = ST_COPY;
+      cp.src = V;
+      cp.dst = Vd;
+      cp.count = Jn * Jn;
+      add(cp);
+    }
+    PView VT = V;
+    VT.rs = Jn;
+    VT.cs = 1;
+    gemm((int)Jn, (int)Jn, (int)Jn, VT, Vc, Ec, 1.0, 0.0, true);
+    gemm((int)Jn, (int)Jn, (int)Jn, VdN, Ec, Vc, -0.5, 1.5, true);
+    PView G = tmp(Jm * Jn);
+    G.rs = 1;
+    G.cs = Jm;
+    gemm((int)Jm, (int)Jn, (int)Jn, M0c, Vc, G, 1.0, 0.0, true);
+    // 3. FP64 Jacobi from V: converges quadratically to the FP64 SVD
+    PView sig = tmp(Jn);
+    {
+      Step st;
+      st.kind = ST_JACOBI;
+      st.m = (int)Jm;
+      st.n = (int)Jn;
+      st.C = G;
+      st.aux1 = V;
+      st.aux2 = sig;
+      st.init_v = 0;
+      st.flops = svd_flops((double)rA, (double)rB);
+      st.bytes = 8.0 * (2.0 * Jm * Jn + 2.0 * Jn * Jn);
+      plan->svd_flops += st.flops;
+      plan->max_jacobi_n = std::max<int64_t>(plan->max_jacobi_n, Jn);
+      add(st);
+    }
+    // truncate + absorb (Eq. "svd"): A_bar = Q_A [U_k s^1/2; 0], B_bar^T = Q' [V_k s^1/2; 0]
+    // with B^T = Q' R'.  The selected factors are written zero-padded straight into
+    // the new tensors, stored column-major (D x kk), i.e. with bonds [new, rem...],
+    // and the Householder products of the two QRs are applied in place.
+    const int nbond = (int)dim.size();
+    dim.push_back(kk);
+    std::vector<int> bi = {nbond};
+    bi.insert(bi.end(), sp.rem_i.begin(), sp.rem_i.end());
+    std::vector<int> bj = {nbond};
+    bj.insert(bj.end(), sp.rem_j.begin(), sp.rem_j.end());
+    int na = new_arena_value(bi);
+    int nbv = new_arena_value(bj);
+    PView Ab = base_view(vals[na]), Bb = base_view(vals[nbv]);
+    {
+      Step st;
+      st.kind = ST_SELECT;
+      st.m = (int)Jm;
+      st.n = (int)Jn;
+      st.k = (int)kk;
+      st.C = G;
+      st.aux1 = V;
+      st.aux2 = sig;
+      // left singular side (rows of the Jacobi matrix) and right side
+      st.out1 = tall ? Ab : Bb;
+      st.out2 = tall ? Bb : Ab;
+      st.count = tall ? DA : DB;     // leading dimension of out1
+      st.init_v = (int)(tall ? DB : DA);  // leading dimension of out2
+      st.bytes = 8.0 * (double)kk * (Jm + Jn + DA + DB);
+      add(st);
+    }
+    auto apply = [&](int64_t mm, const PView& work, const PView& X) {
+      Step st;
+      st.kind = ST_APPLYQ;
+      st.m = (int)mm;
+      st.n = (int)dab;
+      st.k = (int)kk;
+      st.work = work;
+      st.C = X;
+      st.flops = 0.0;
+      st.bytes = 8.0 * (mm * dab + 2.0 * mm * kk);
+      add(st);
+    };
+    if (DA > dab) apply(DA, workA, Ab);
+    if (DB > dab) apply(DB, workB, Bb);
+    // the paper's absorb contractions: (D_A x r_A)(r_A x k) and (k x r_B)(r_B x D_B)
+    plan->gemm_flops += 2.0 * DA * rA * (double)kk + 2.0 * kk * rB * (double)DB;
+    rescale(na);
+    rescale(nbv);
+    for (auto& t : trel) arena.release(t.first, t.second);
+    for (int t : tmps) release_value(t);
+    release_value(ia0);
+    release_value(ib0);
+    cur[i] = na;
+    cur[j] = nbv;
+    record(i, na);
+    record(j, nbv);
+    plan->n_compressions++;
+    return "";
+  }
+};
+
+}  // namespace
+
+std::string validate_tree(const Structure& s, const std::vector<int32_t>& ops, int n_inputs) {
+  const int nt = (int)s.bonds.size();
+  if (n_inputs != nt) return "tree inputs != network tensors";
+  if (ops.size() % 4) return "ops array is not a multiple of 4";
+  std::unordered_set<int> live;
+  for (int t = 0; t < nt; ++t) live.insert(t);
+  int next = nt;
+  const size_t nops = ops.size() / 4;
+  for (size_t r = 0; r < nops; ++r) {
+    const int kind = ops[4 * r], i = ops[4 * r + 1], j = ops[4 * r + 2], k = ops[4 * r + 3];
+    if (i == j || !live.count(i) || !live.count(j))
+      return "op " + std::to_string(r) + ": ids " + std::to_string(i) + ", " + std::to_string(j) +
+             " are not two live tensors";
+    if (kind == 0) {
+      if (k != next) return "op " + std::to_string(r) + ": C must create id " + std::to_string(next);
+      live.erase(i);
+      live.erase(j);
+      live.insert(k);
+      ++next;
+    } else if (kind != 1) {
+      return "op " + std::to_string(r) + ": unknown kind";
+    }
+  }
+  if (live.size() != 1) return "tree leaves " + std::to_string(live.size()) + " tensors (need 1)";
+  return "";
+}
+
+std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int n_inputs, int chi,
+                       int prec, Plan* out) {
+  std::string err = validate_tree(s, ops, n_inputs);
+  if (!err.empty()) return err;
+  if (chi < 1) return "chi must be >= 1";
+  *out = Plan();
+  out->chi = chi;
+  out->prec = prec;
+  Builder bld{s, chi, out};
+  bld.dim = s.bond_dims;
+  const int nt = (int)s.bonds.size();
+  for (int t = 0; t < nt; ++t) {
+    Value v;
+    v.bonds = s.bonds[t];
+    v.size = prod_dims(v.bonds, bld.dim);
+    v.buf = BUF_INPUT;
+    v.off = s.in_off[t];
+    v.bs = s.in_total;
+    bld.vals.push_back(v);
+    bld.cur[t] = t;
+    bld.op_index = -1;
+    bld.record(t, t);
+  }
+  const size_t nops = ops.size() / 4;
+  for (size_t r = 0; r < nops; ++r) {
+    bld.op_index = (int)r;
+    const int kind = ops[4 * r], i = ops[4 * r + 1], j = ops[4 * r + 2], k = ops[4 * r + 3];
+    std::string e = (kind == 0) ? bld.contract(i, j, k) : bld.compress(i, j);
+    if (!e.empty()) return "op " + std::to_string(r) + ": " + e;
+  }
+  // the single remaining tensor must be a scalar
+  if (bld.cur.size() != 1) return "tree does not end in one tensor";
+  const Value& root = bld.vals[bld.cur.begin()->second];
+  if (root.size != 1) return "final tensor has open bonds";
+  out->final_scalar = bld.base_view(root);
+  out->arena_units = bld.arena.peak();
+  Step fin;
+  fin.kind = ST_FINAL;
+  fin.C = out->final_scalar;
+  out->steps.push_back(fin);
+  return "";
+}
+
+}  // namespace tnp

@@ -1,0 +1,238 @@
+"""Thin ctypes binding of ``libtn.so`` (include/tn.h): argument marshalling only.
+
+Every step of the contraction runs in the library's CUDA kernels; this module
+converts Python objects to plain pointers and sizes and raises
+:class:`TNError` on any non-OK status.  It never computes a result itself and
+has no CPU fallback: if ``libtn.so`` is missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtn.so")
+
+TN_F64, TN_TF32, TN_BF16, TN_TF32X3 = 0, 1, 2, 3
+PREC = {"f64": TN_F64, "tf32": TN_TF32, "bf16": TN_BF16, "tf32x3": TN_TF32X3}
+
+STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_EFORMAT", -3: "TN_ESHAPE", -4: "TN_ENOMEM",
+          -5: "TN_ECUDA", -6: "TN_ETIMEOUT", -7: "TN_ENONFINITE", -8: "TN_ESTATE", -9: "TN_ENOCONV"}
+
+
+class TNError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class NetworkDesc(C.Structure):
+    _fields_ = [("n_bonds", C.c_int32), ("bond_dims", C.POINTER(C.c_int64)),
+                ("n_tensors", C.c_int32), ("ndims", C.POINTER(C.c_int32)),
+                ("bond_ids", C.POINTER(C.c_int32)), ("data", C.POINTER(C.POINTER(C.c_double)))]
+
+
+class TreeDesc(C.Structure):
+    _fields_ = [("n_inputs", C.c_int32), ("n_ops", C.c_int32), ("ops", C.POINTER(C.c_int32))]
+
+
+class PlanStats(C.Structure):
+    _fields_ = [("n_contractions", C.c_int64), ("n_compressions", C.c_int64),
+                ("gemm_flops", C.c_double), ("qr_flops", C.c_double), ("svd_flops", C.c_double),
+                ("permute_bytes", C.c_double), ("peak_bytes", C.c_double),
+                ("kernel_launches", C.c_int64)]
+
+
+# every symbol include/tn.h declares, with its ctypes signature
+SIGNATURES = {
+    "tn_version": (C.c_char_p, []),
+    "tn_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
+    "tn_destroy": (None, [C.c_void_p]),
+    "tn_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tn_load_network": (C.c_int, [C.c_void_p, C.POINTER(NetworkDesc), C.POINTER(C.c_int)]),
+    "tn_load_network_file": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int)]),
+    "tn_set_network_data": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.c_int]),
+    "tn_load_tree": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(TreeDesc), C.POINTER(C.c_int)]),
+    "tn_load_tree_file": (C.c_int, [C.c_void_p, C.c_int, C.c_char_p, C.POINTER(C.c_int)]),
+    "tn_contract_approx": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                     C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "tn_plan_stats_get": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(PlanStats)]),
+    "tn_debug_tensor": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.c_int, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "tn_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "tn_kernel_times": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p),
+                                  C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "tn_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+_LIB: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    """Load libtn.so (built by ``paper_2206_07044_gb300.build``); raise if absent."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2206_07044_gb300.build.build() first "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._L = lib()
+        h = C.c_void_p()
+        rc = self._L.tn_create(C.byref(h), int(device))
+        if rc != 0:
+            raise TNError(rc, f"tn_create(device={device}) failed (no CUDA device?)")
+        self._h = h
+        self.device = device
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._L.tn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int) -> None:
+        if rc != 0:
+            raise TNError(rc, self._L.tn_last_error(self._h).decode())
+
+    def set_stream(self, stream) -> None:
+        self._check(self._L.tn_set_stream(self._h, C.c_void_p(_stream_handle(stream))))
+
+    def load_network(self, net) -> int:
+        """net: an object with bond_dims, bonds (per tensor) and data (float64 arrays)."""
+        dims = np.ascontiguousarray(net.bond_dims, dtype=np.int64)
+        ndims = np.array([len(b) for b in net.bonds], dtype=np.int32)
+        ids = np.ascontiguousarray(np.concatenate([np.asarray(b, dtype=np.int32) for b in net.bonds])
+                                   if sum(ndims) else np.zeros(1, np.int32), dtype=np.int32)
+        arrays = [np.ascontiguousarray(d, dtype=np.float64) for d in net.data]
+        ptrs = (C.POINTER(C.c_double) * len(arrays))(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrays])
+        desc = NetworkDesc(len(dims), dims.ctypes.data_as(C.POINTER(C.c_int64)), len(arrays),
+                           ndims.ctypes.data_as(C.POINTER(C.c_int32)), ids.ctypes.data_as(C.POINTER(C.c_int32)),
+                           ptrs)
+        out = C.c_int()
+        self._check(self._L.tn_load_network(self._h, C.byref(desc), C.byref(out)))
+        return out.value
+
+    def load_network_file(self, path: str) -> int:
+        out = C.c_int()
+        self._check(self._L.tn_load_network_file(self._h, path.encode(), C.byref(out)))
+        return out.value
+
+    def set_network_data(self, net_id: int, tensors: Sequence, on_device: bool = False) -> None:
+        """Replace a network's entries: host float64 arrays, or device pointers / CUDA tensors."""
+        keep = []
+        ptrs = []
+        for t in tensors:
+            if on_device:
+                ptrs.append(int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t))
+            elif hasattr(t, "data_ptr"):
+                # a host torch tensor (e.g. pinned): its storage is passed as is
+                if not (t.is_contiguous() and str(t.dtype) == "torch.float64" and t.device.type == "cpu"):
+                    raise ValueError("host tensors must be contiguous float64 CPU tensors")
+                keep.append(t)
+                ptrs.append(int(t.data_ptr()))
+            else:
+                a = np.ascontiguousarray(t, dtype=np.float64)
+                keep.append(a)
+                ptrs.append(a.ctypes.data)
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+        self._check(self._L.tn_set_network_data(self._h, int(net_id), arr, 1 if on_device else 0))
+        self._keep_alive = keep
+
+    def load_tree(self, net_id: int, tree) -> int:
+        ops = np.ascontiguousarray(tree.as_int_array(), dtype=np.int32)
+        if ops.size == 0:
+            ops = np.zeros((0, 4), np.int32)
+        desc = TreeDesc(int(tree.n_inputs), int(ops.shape[0]),
+                        ops.ctypes.data_as(C.POINTER(C.c_int32)) if ops.size else None)
+        out = C.c_int()
+        self._check(self._L.tn_load_tree(self._h, int(net_id), C.byref(desc), C.byref(out)))
+        return out.value
+
+    def load_tree_file(self, net_id: int, path: str) -> int:
+        out = C.c_int()
+        self._check(self._L.tn_load_tree_file(self._h, int(net_id), path.encode(), C.byref(out)))
+        return out.value
+
+    def contract(self, inst_ids: Iterable[int], chi: int, prec="f64") -> Tuple[np.ndarray, np.ndarray]:
+        """(log|Z|, sign) per instance, computed on the GPU."""
+        ids = np.ascontiguousarray(list(inst_ids), dtype=np.int32)
+        n = len(ids)
+        logz = np.zeros(n, dtype=np.float64)
+        sign = np.zeros(n, dtype=np.int32)
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        self._check(self._L.tn_contract_approx(self._h, n, ids.ctypes.data_as(C.POINTER(C.c_int)), int(chi), p,
+                                               logz.ctypes.data_as(C.POINTER(C.c_double)),
+                                               sign.ctypes.data_as(C.POINTER(C.c_int))))
+        return logz, sign
+
+    def debug_tensor(self, inst_ids: Sequence[int], which: int, chi: int, stop_op: int, tensor_id: int,
+                     prec="f64") -> Tuple[np.ndarray, List[int]]:
+        """Tensor `tensor_id` of instance inst_ids[which] after tree op `stop_op` (GPU-computed).
+
+        Returns (array shaped by its storage order, bond ids in that order).
+        """
+        ids = np.ascontiguousarray(list(inst_ids), dtype=np.int32)
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        nd = C.c_int32()
+        bonds = (C.c_int32 * 24)()
+        dims = (C.c_int64 * 24)()
+        args = (self._h, len(ids), ids.ctypes.data_as(C.POINTER(C.c_int)), int(which), int(chi), p, int(stop_op),
+                int(tensor_id))
+        self._check(self._L.tn_debug_tensor(*args, None, 0, C.byref(nd), bonds, dims))
+        shape = [int(dims[a]) for a in range(nd.value)]
+        out = np.zeros(int(np.prod(shape, dtype=np.int64)), dtype=np.float64)
+        self._check(self._L.tn_debug_tensor(*args, out.ctypes.data_as(C.POINTER(C.c_double)), out.size,
+                                            C.byref(nd), bonds, dims))
+        return out.reshape(shape), [int(bonds[a]) for a in range(nd.value)]
+
+    def plan_stats(self, inst_id: int, chi: int, prec="f64") -> Dict[str, float]:
+        st = PlanStats()
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        self._check(self._L.tn_plan_stats_get(self._h, int(inst_id), int(chi), p, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in PlanStats._fields_}
+
+    def profile(self, enable: bool) -> None:
+        self._check(self._L.tn_profile_enable(self._h, 1 if enable else 0))
+
+    def kernel_times(self) -> List[Tuple[str, int, float]]:
+        cap = 32
+        names = (C.c_char_p * cap)()
+        launches = (C.c_int64 * cap)()
+        ms = (C.c_double * cap)()
+        n = self._L.tn_kernel_times(self._h, cap, names, launches, ms)
+        return [(names[i].decode(), int(launches[i]), float(ms[i])) for i in range(min(n, cap))]
+
+
+def version() -> str:
+    return lib().tn_version().decode()
