@@ -171,6 +171,32 @@ int tn_debug_tensor(tn_ctx* ctx, int n_inst, const int* inst_ids, int which, int
 int tn_profile_enable(tn_ctx* ctx, int enable);
 int tn_kernel_times(tn_ctx* ctx, int cap, const char** names, int64_t* launches, double* total_ms);
 
+/* Approximate contraction of ONE instance without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- a plug-in inside a host application whose own
+ * allocator has already reserved the device memory, or code on a
+ * latency-critical path where cudaMalloc / cudaFree would synchronise the
+ * whole device.  Every device buffer (the copied inputs, the schedule's arena,
+ * the QR / Jacobi / log-norm scratch, the result words) is carved from one
+ * file-scope __device__ array of 8 MiB that every GPU loading the library
+ * holds until the process exits; an instance needing more is rejected with
+ * TN_ENOMEM and a message giving both sizes, before any GPU work.
+ *   net, tree   as for tn_load_network / tn_load_tree (host data, copied)
+ *   chi         >= 1; the FP64 form is used
+ *   cuda_stream the stream to run on (NULL = legacy default), on the current
+ *               device; the call synchronises it before returning
+ *   outputs     *logabsz_out = ln|Z|, *sign_out in {-1, 0, +1} (host)
+ *   err_msg     optional host buffer (err_cap bytes) for a message
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * on a device share the one array (what must start at zero is cleared on
+ * each call), so calls that overlap on the GPU -- on two streams or from two
+ * threads -- race; serialise them.  Results equal tn_contract_approx's for a
+ * batch of one (same schedule, same kernels). */
+int tn_contract_approx_noalloc(const tn_network_desc* net, const tn_tree_desc* tree, int chi,
+                               void* cuda_stream, double* logabsz_out, int* sign_out, char* err_msg,
+                               size_t err_cap);
+
 /* Message for the last non-OK status returned on this context (never NULL). */
 const char* tn_last_error(const tn_ctx* ctx);
 

@@ -67,6 +67,8 @@ SIGNATURES = {
     "tn_kernel_times": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p),
                                   C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "tn_last_error": (C.c_char_p, [C.c_void_p]),
+    "tn_contract_approx_noalloc": (C.c_int, [C.POINTER(NetworkDesc), C.POINTER(TreeDesc), C.c_int, C.c_void_p,
+                                             C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_char_p, C.c_size_t]),
 }
 
 _LIB: Optional[C.CDLL] = None
