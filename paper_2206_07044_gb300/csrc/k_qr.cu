@@ -46,6 +46,10 @@ __device__ double block_sum(double x, double* red) {
   return r;
 }
 
+// kSmem: this CTA's columns live in shared memory for the whole factorisation
+// (reflectors are also written to global memory for the other CTAs and for
+// apply_q); otherwise they are updated in place in the global working copy.
+template <bool kSmem>
 __global__ void __launch_bounds__(kThreads) qr_cluster_kernel(int m, int n, View A, double* work,
                                                               int64_t work_bs, double* taus,
                                                               ViewW R) {
@@ -57,19 +61,27 @@ __global__ void __launch_bounds__(kThreads) qr_cluster_kernel(int m, int n, View
   double* W = work + (int64_t)b * work_bs;
   double* tau_b = taus + (int64_t)b * n;
   const double* a = A.p + (int64_t)b * A.bs;
-  extern __shared__ double vs[];
+  extern __shared__ double sm[];
   __shared__ double red[32];
-  const bool stage_v = (m <= kVSmem);
+  const int nc_max = (n + P - 1) / P;
+  double* colbuf = sm;                                       // kSmem: nc_max columns of length m
+  double* vs = kSmem ? sm + (size_t)nc_max * m : sm;         // reflector staging (m <= kVSmem)
+  const bool stage_v = kSmem || (m <= kVSmem);
+  auto col_of = [&](int c) -> double* {
+    return kSmem ? colbuf + (size_t)((c - rank) / P) * m : W + (int64_t)c * m;
+  };
 
   // working copy of this CTA's columns
-  for (int c = rank; c < n; c += P)
-    for (int r = tid; r < m; r += blockDim.x) W[(int64_t)c * m + r] = a[(int64_t)r * A.rs + (int64_t)c * A.cs];
+  for (int c = rank; c < n; c += P) {
+    double* dst = col_of(c);
+    for (int r = tid; r < m; r += blockDim.x) dst[r] = a[(int64_t)r * A.rs + (int64_t)c * A.cs];
+  }
   __syncthreads();
 
   const int rmin = m < n ? m : n;
   for (int j = 0; j < rmin; ++j) {
     if (j % P == rank) {
-      double* x = W + (int64_t)j * m;
+      double* x = col_of(j);
       double part = 0.0;
       for (int r = j + 1 + tid; r < m; r += blockDim.x) part += x[r] * x[r];
       const double sigma = block_sum(part, red);
@@ -80,7 +92,12 @@ __global__ void __launch_bounds__(kThreads) qr_cluster_kernel(int m, int n, View
         const double beta = (alpha <= 0.0) ? nrm : -nrm;
         tau = (beta - alpha) / beta;
         const double scale = 1.0 / (alpha - beta);
-        for (int r = j + 1 + tid; r < m; r += blockDim.x) x[r] *= scale;
+        double* g = W + (int64_t)j * m;
+        for (int r = j + 1 + tid; r < m; r += blockDim.x) {
+          const double v = x[r] * scale;
+          x[r] = v;
+          if (kSmem) g[r] = v;   // publish the reflector
+        }
         __syncthreads();
         if (tid == 0) x[j] = beta;
       }
@@ -99,12 +116,12 @@ __global__ void __launch_bounds__(kThreads) qr_cluster_kernel(int m, int n, View
       int c0 = j + 1 + ((rank - (j + 1)) % P + P) % P;
       int ncol = (c0 < n) ? (n - 1 - c0) / P + 1 : 0;
       for (int q = warp; q < ncol; q += nwarps) {
-        double* col = W + (int64_t)(c0 + q * P) * m + j;
+        double* col = col_of(c0 + q * P) + j;
         double d = 0.0;
         if (stage_v) {
-          for (int r = lane; r < len; r += 32) d += vs[r] * col[r];
+          for (int r = lane; r < len; r += 32) d = fma(vs[r], col[r], d);
         } else {
-          for (int r = lane; r < len; r += 32) d += (r == 0 ? 1.0 : __ldcg(v + j + r)) * col[r];
+          for (int r = lane; r < len; r += 32) d = fma(r == 0 ? 1.0 : __ldcg(v + j + r), col[r], d);
         }
         d = warp_sum(d) * tau;
         if (stage_v) {
@@ -116,12 +133,17 @@ __global__ void __launch_bounds__(kThreads) qr_cluster_kernel(int m, int n, View
     }
     __syncthreads();
   }
-  // R: rows 0..rmin-1 of this CTA's columns; the diagonal holds beta
+  // R: rows 0..rmin-1 of this CTA's columns (the diagonal holds beta); with
+  // kSmem the columns (R above, reflectors below the diagonal) go back to W
   double* rr = R.p + (int64_t)b * R.bs;
   for (int c = rank; c < n; c += P) {
-    const double* col = W + (int64_t)c * m;
+    const double* col = col_of(c);
     for (int i = tid; i < rmin; i += blockDim.x)
       rr[(int64_t)i * R.rs + (int64_t)c * R.cs] = (i <= c) ? col[i] : 0.0;
+    if (kSmem) {
+      double* g = W + (int64_t)c * m;
+      for (int r = tid; r < m; r += blockDim.x) g[r] = col[r];
+    }
   }
 }
 
@@ -182,20 +204,17 @@ cudaError_t apply_q_f64(int m, int n, const double* work, int64_t work_bs, doubl
   return cudaGetLastError();
 }
 
-cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW R, int batch,
-                     cudaStream_t s) {
-  if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
-  if (batch > 65535) return cudaErrorInvalidValue;
-  // tau scratch sits after the batch of working copies
-  double* taus = work + (int64_t)batch * work_bs;
-  int P = (n + 15) / 16;
-  if (P > 8) P = 8;
-  if (P < 1) P = 1;
-  size_t smem = (m <= kVSmem) ? (size_t)m * sizeof(double) : 0;
+namespace {
+
+constexpr size_t kQrSmemCap = 210 * 1024;
+
+template <bool kSmem>
+cudaError_t launch_qr(int P, int m, int n, View A, double* work, int64_t work_bs, double* taus, ViewW R,
+                      int batch, cudaStream_t s, size_t smem) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(qr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kVSmem * (int)sizeof(double));
+    cudaFuncSetAttribute(qr_cluster_kernel<kSmem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemCap);
+    cudaFuncSetAttribute(qr_cluster_kernel<kSmem>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     attr_done = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -210,7 +229,41 @@ cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, qr_cluster_kernel, m, n, A, work, work_bs, taus, R);
+  if (P > 8) {
+    // a 16-CTA cluster must fit in one GPC; fall back to 8 when it cannot be placed
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, qr_cluster_kernel<kSmem>, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      return cudaErrorNotSupported;
+    }
+  }
+  return cudaLaunchKernelEx(&cfg, qr_cluster_kernel<kSmem>, m, n, A, work, work_bs, taus, R);
+}
+
+}  // namespace
+
+cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW R, int batch,
+                     cudaStream_t s) {
+  if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  // tau scratch sits after the batch of working copies
+  double* taus = work + (int64_t)batch * work_bs;
+  // cluster size: about 16 columns per CTA, up to 16 CTAs (non-portable size)
+  int P = (n + 15) / 16;
+  if (P > 16) P = 16;
+  if (P < 1) P = 1;
+  for (; P >= 1; P = (P > 8 ? 8 : P)) {
+    const int nc = (n + P - 1) / P;
+    const size_t smem_cols = ((size_t)nc * m + (size_t)m) * sizeof(double);
+    cudaError_t e;
+    if (smem_cols <= kQrSmemCap)
+      e = launch_qr<true>(P, m, n, A, work, work_bs, taus, R, batch, s, smem_cols);
+    else
+      e = launch_qr<false>(P, m, n, A, work, work_bs, taus, R, batch, s,
+                           (m <= kVSmem) ? (size_t)m * sizeof(double) : 0);
+    if (e != cudaErrorNotSupported || P <= 8) return e;
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace tnk

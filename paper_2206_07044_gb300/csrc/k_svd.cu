@@ -81,6 +81,7 @@ struct JacArgs {
   T sig_tol;        // ... and the pair is not yet converged iff |gamma| > sig_tol * sqrt(alpha beta)
   T floor_rel;      // columns with |g| <= floor_rel * |G|_F are left alone
   T floor2;         // (set in the kernel) floor_rel^2 * |G|_F^2
+  unsigned long long* sweep_ctr;  // optional: total sweeps run, summed over matrices
 };
 
 // Squared Frobenius norm of G.  Each CTA writes its partial sum to its own
@@ -199,7 +200,9 @@ __global__ void __launch_bounds__(kThreads) block_jacobi_kernel(JacArgs<T> p) {
   cl.sync();
 
   bool converged = (n < 2);
+  int sweeps_run = 0;
   for (int sweep = 0; sweep < p.max_sweeps && !converged; ++sweep) {
+    ++sweeps_run;
     if (rank == 0 && threadIdx.x == 0) cnt[(sweep + 1) % 3] = 0;
     if (threadIdx.x == 0) sig_rot_s = 0;
     int sig_rot = 0;
@@ -284,6 +287,7 @@ __global__ void __launch_bounds__(kThreads) block_jacobi_kernel(JacArgs<T> p) {
     converged = (__ldcg(cnt + (sweep % 3)) == 0);
   }
   if (!converged && p.status && rank == 0 && threadIdx.x == 0) atomicExch(p.status + bidx, -9);
+  if (p.sweep_ctr && rank == 0 && threadIdx.x == 0) atomicAdd(p.sweep_ctr, (unsigned long long)sweeps_run);
   if (p.sig) {
     double* sig = p.sig + (int64_t)bidx * p.sig_bs;
     for (int c = rank * nwarps + warp; c < n; c += P * nwarps) {
@@ -323,7 +327,9 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
   if (rank == 0 && threadIdx.x < 3) cnt[threadIdx.x] = 0;
   cl.sync();
   bool converged = (n < 2);
+  int sweeps_run = 0;
   for (int sweep = 0; sweep < p.max_sweeps && !converged; ++sweep) {
+    ++sweeps_run;
     if (rank == 0 && threadIdx.x == 0) cnt[(sweep + 1) % 3] = 0;
     int sig_rot = 0;
     for (int rnd = 0; rnd < np - 1; ++rnd) {
@@ -354,6 +360,7 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
     converged = (__ldcg(cnt + (sweep % 3)) == 0);
   }
   if (!converged && p.status && rank == 0 && threadIdx.x == 0) atomicExch(p.status + bidx, -9);
+  if (p.sweep_ctr && rank == 0 && threadIdx.x == 0) atomicAdd(p.sweep_ctr, (unsigned long long)sweeps_run);
   if (p.sig) {
     double* sig = p.sig + (int64_t)bidx * p.sig_bs;
     for (int c = gw; c < n; c += nw) {
@@ -383,10 +390,18 @@ cudaError_t launch_jacobi(const JacArgs<T>& a, int batch, cudaStream_t s) {
   if (a.m < a.n || batch > 65535) return cudaErrorInvalidValue;
   cudaError_t ze = cudaMemsetAsync(a.ws, 0, sizeof(int) * kWsInts * (size_t)batch, s);
   if (ze != cudaSuccess) return ze;
-  // cluster size: about one block pair of >= 8 columns per CTA, at most 8 CTAs
+  // cluster size: about one block pair of >= 8 columns per CTA, up to 16 CTAs
+  // (non-portable; falls back to 8 when a 16-CTA cluster cannot be placed)
   int P = a.n / 16;
-  if (P > 8) P = 8;
+  if (P > 16) P = 16;
   if (P < 1) P = 1;
+  if (P > 8) {
+    static bool np_set = false;
+    if (!np_set) {
+      cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      np_set = true;
+    }
+  }
   size_t smem = block_smem<T>(a.m, a.n, P);
   const bool use_block = smem <= kSmemCap;
   cudaLaunchConfig_t cfg = {};
@@ -407,8 +422,20 @@ cudaError_t launch_jacobi(const JacArgs<T>& a, int batch, cudaStream_t s) {
       attr_set = true;
     }
     cfg.dynamicSmemBytes = smem;
+    if (P > 8) {
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, block_jacobi_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        P = 8;
+        cfg.gridDim = dim3(P, batch, 1);
+        attr[0].val.clusterDim.x = P;
+        cfg.dynamicSmemBytes = block_smem<T>(a.m, a.n, P);
+        if (cfg.dynamicSmemBytes > kSmemCap) goto fallback;
+      }
+    }
     return cudaLaunchKernelEx(&cfg, block_jacobi_kernel<T>, a);
   }
+fallback:
   P = a.n / 64;
   if (P > 8) P = 8;
   if (P < 1) P = 1;
@@ -482,21 +509,22 @@ int grid1d(int64_t n) {
 }  // namespace
 
 cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64_t v_bs, int* ws,
-                           DevState st, int batch, cudaStream_t s) {
+                           DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr) {
   // a preconditioner: running out of sweeps is not an error (the FP64 stage decides)
   JacArgs<float> a{m, n, G, g_bs, V, v_bs, nullptr, 0, ws, nullptr, 1, 60,
-                   4.0f * (float)m * FLT_EPSILON, 1e-4f, 1e-6f, 0.0f};
+                   4.0f * (float)m * FLT_EPSILON, 1e-4f, 1e-6f, 0.0f, sweep_ctr};
   return launch_jacobi(a, batch, s);
 }
 
 cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int64_t v_bs, double* sig,
-                           int64_t sig_bs, int* ws, DevState st, int init_v, int batch, cudaStream_t s) {
+                           int64_t sig_bs, int* ws, DevState st, int init_v, int batch, cudaStream_t s,
+                           unsigned long long* sweep_ctr) {
   // rotate down to sqrt(m) eps (the cut's subspace error is that over the gap);
   // convergence is judged by the looser sig_tol, so rounding-level rotations
   // never keep the sweep loop alive
   const double rt = sqrt((double)(m > 16 ? m : 16));
   JacArgs<double> a{m, n, G, g_bs, V, v_bs, sig, sig_bs, ws, st.status, init_v, 60,
-                    rt * DBL_EPSILON, 1e-9, 1e-14, 0.0};
+                    rt * DBL_EPSILON, 1e-9, 1e-14, 0.0, sweep_ctr};
   return launch_jacobi(a, batch, s);
 }
 

@@ -80,8 +80,13 @@ struct tn_ctx {
   unsigned long long* maxbits = nullptr;
   double* out_log = nullptr;
   int* out_sign = nullptr;
+  // side stream for steps that may overlap the main stream, and fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  unsigned long long* sweeps = nullptr;  // [2] device: Jacobi sweeps run (FP32, FP64) while profiling
   // profiling
   bool profile = false;
+  unsigned long long prof_sweeps[2] = {0, 0};
   int64_t prof_launches[kNumFamily] = {0};
   double prof_ms[kNumFamily] = {0};
 };
@@ -309,6 +314,17 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   cudaMemsetAsync(c->expo, 0, sizeof(long long) * batch, s);
   cudaMemsetAsync(c->status, 0, sizeof(int) * batch, s);
   tnk::DevState ds{c->expo, c->status};
+  if (!c->side) {
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, TN_ECUDA, "side stream creation failed");
+  }
+  if (c->profile && !c->sweeps && cudaMalloc(&c->sweeps, 2 * sizeof(unsigned long long)) != cudaSuccess)
+    return fail(c, TN_ENOMEM, "profiling counters");
+  if (c->profile) cudaMemsetAsync(c->sweeps, 0, 2 * sizeof(unsigned long long), s);
+  unsigned long long* sw32 = c->profile ? c->sweeps : nullptr;
+  unsigned long long* sw64 = c->profile ? c->sweeps + 1 : nullptr;
   auto ptr = [&](const tnp::PView& v) -> double* {
     return v.buf == tnp::BUF_INPUT ? c->inbuf + v.off : c->arena + v.off * batch;
   };
@@ -320,6 +336,15 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   for (const tnp::Step& stp : plan.steps) {
     if (stop_op >= 0 && (stp.op_index > stop_op || stp.kind == tnp::ST_FINAL)) break;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (stp.join) cudaStreamWaitEvent(s, c->ev_join, 0);
+    // a side-lane step forks from the main stream; profiling keeps everything on one stream
+    const bool on_side = stp.lane == 1 && !c->profile;
+    cudaStream_t ms = s;
+    if (on_side) {
+      cudaEventRecord(c->ev_fork, s);
+      cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+      s = c->side;
+    }
     if (c->profile) {
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
@@ -339,7 +364,7 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
         break;
       case tnp::ST_JACOBI:
         e = tnk::jacobi_svd_f64(stp.m, stp.n, ptr(stp.C), stp.C.bs, ptr(stp.aux1), stp.aux1.bs,
-                                ptr(stp.aux2), stp.aux2.bs, c->jac_ws, ds, stp.init_v, batch, s);
+                                ptr(stp.aux2), stp.aux2.bs, c->jac_ws, ds, stp.init_v, batch, s, sw64);
         break;
       case tnp::ST_TO_F32:
         e = tnk::convert_f64_to_f32(ptr(stp.src), stp.count, stp.src.bs, reinterpret_cast<float*>(ptr(stp.dst)),
@@ -347,7 +372,7 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
         break;
       case tnp::ST_JACOBI32:
         e = tnk::jacobi_svd_f32(stp.m, stp.n, reinterpret_cast<float*>(ptr(stp.C)), stp.fbs_src,
-                                reinterpret_cast<float*>(ptr(stp.aux1)), stp.fbs_dst, c->jac_ws, ds, batch, s);
+                                reinterpret_cast<float*>(ptr(stp.aux1)), stp.fbs_dst, c->jac_ws, ds, batch, s, sw32);
         break;
       case tnp::ST_COPY:
         e = cudaMemcpyAsync(ptr(stp.dst), ptr(stp.src), sizeof(double) * (size_t)stp.dst.bs * batch,
@@ -383,6 +408,10 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
       evs.push_back({e0, e1});
       ev_family.push_back(stp.kind);
     }
+    if (on_side) {
+      cudaEventRecord(c->ev_join, s);
+      s = ms;
+    }
   }
   if (stop_op >= 0) {
     e = cudaStreamSynchronize(s);
@@ -394,8 +423,13 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   e = cudaMemcpyAsync(hl.data(), c->out_log, sizeof(double) * batch, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), c->out_sign, sizeof(int) * batch, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), c->status, sizeof(int) * batch, cudaMemcpyDeviceToHost, s);
+  unsigned long long hsw[2] = {0, 0};
+  if (e == cudaSuccess && c->profile)
+    e = cudaMemcpyAsync(hsw, c->sweeps, sizeof(hsw), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+  c->prof_sweeps[0] += hsw[0];
+  c->prof_sweeps[1] += hsw[1];
   for (size_t q = 0; q < evs.size(); ++q) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, evs[q].first, evs[q].second);
@@ -455,6 +489,10 @@ void tn_destroy(tn_ctx* c) {
   cudaFree(c->maxbits);
   cudaFree(c->out_log);
   cudaFree(c->out_sign);
+  cudaFree(c->sweeps);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 
@@ -681,6 +719,7 @@ int tn_profile_enable(tn_ctx* c, int enable) {
     c->prof_launches[f] = 0;
     c->prof_ms[f] = 0.0;
   }
+  c->prof_sweeps[0] = c->prof_sweeps[1] = 0;
   return TN_OK;
 }
 
@@ -693,6 +732,17 @@ int tn_kernel_times(tn_ctx* c, int cap, const char** names, int64_t* launches, d
       if (names) names[n] = kFamily[f];
       if (launches) launches[n] = c->prof_launches[f];
       if (total_ms) total_ms[n] = c->prof_ms[f];
+    }
+    ++n;
+  }
+  // pseudo-families: Jacobi sweeps run (launches = sweeps summed over matrices, time 0)
+  const char* sw_names[2] = {"sweeps:jacobi_f32", "sweeps:jacobi_f64"};
+  for (int q = 0; q < 2; ++q) {
+    if (!c->prof_sweeps[q]) continue;
+    if (n < cap) {
+      if (names) names[n] = sw_names[q];
+      if (launches) launches[n] = (int64_t)c->prof_sweeps[q];
+      if (total_ms) total_ms[n] = 0.0;
     }
     ++n;
   }

@@ -45,12 +45,13 @@ cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW 
 // accumulated rotations (V = I first when init_v), sig the FP64 column norms
 // sigma_i (unsorted).  ws: 64 ints per batch of scratch.  Sets st.status[b] = -9
 // if the bounded sweep loop ran out.
+// sweep_ctr (optional, device): the sweeps run are added to it.
 cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int64_t v_bs,
                            double* sig, int64_t sig_bs, int* ws, DevState st, int init_v,
-                           int batch, cudaStream_t s);
+                           int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr);
 // The FP32 preconditioning pass (V = I first); never sets a status.
 cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64_t v_bs, int* ws,
-                           DevState st, int batch, cudaStream_t s);
+                           DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr);
 // y = (float) x and y1 (= y2 when given) = (double) x, n elements per batch.
 cudaError_t convert_f64_to_f32(const double* x, int64_t n, int64_t xbs, float* y, int64_t ybs,
                                int batch, cudaStream_t s);
@@ -81,5 +82,15 @@ cudaError_t finalize_f64(const double* x, int64_t bs, DevState st, double* out_l
 
 // Fill a batch of n x n column-major matrices with the identity.
 cudaError_t set_identity_f64(double* V, int n, int64_t bs, int batch, cudaStream_t s);
+
+// Mixed-precision GEMM on tcgen05 tensor cores (TF32 or BF16 inputs, FP32
+// accumulation in TMEM, TMA-fed): C = alpha * A * B written as FP64.
+// workspace: device scratch of gemm_tc_workspace_bytes(...) bytes (16-byte
+// aligned) for the K-major staged operands; err: device int set to 1 if a
+// bounded wait inside the kernel ran out.
+// mode: 0 = TF32, 1 = BF16, 2 = split TF32 (3 products, about FP32 accuracy).
+size_t gemm_tc_workspace_bytes(int m, int n, int k, int mode, int batch);
+cudaError_t gemm_tc(int m, int n, int k, double alpha, View A, View B, ViewW C, int batch, int mode,
+                    void* workspace, size_t ws_bytes, int* err, cudaStream_t s);
 
 }  // namespace tnk

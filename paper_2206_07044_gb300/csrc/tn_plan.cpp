@@ -351,6 +351,7 @@ struct Builder {
       std::swap(Bt.rs, Bt.cs);
       Step st;
       st.kind = ST_QR;
+      st.lane = 1;   // independent of the QR of A: overlaps it on the side stream
       st.m = (int)DB;
       st.n = (int)dab;
       st.A = Bt;
@@ -373,6 +374,7 @@ struct Builder {
     PView M0 = tmp(rA * rB);
     if (tall) { M0.rs = 1; M0.cs = rA; } else { M0.rs = rB; M0.cs = 1; }
     gemm((int)rA, (int)rB, (int)dab, RA, LB, M0);
+    if (DB > dab) plan->steps.back().join = 1;
     PView M0c = M0;  // the same buffer as a Jm x Jn column-major view
     M0c.rs = 1;
     M0c.cs = Jm;

@@ -55,6 +55,8 @@ struct Step {
   double alpha = 1.0, beta = 0.0;  // gemm: C = alpha A B + beta C
   int init_v = 1;          // jacobi: start from V = I
   int64_t fbs_src = 0, fbs_dst = 0;  // per-instance strides in floats for FP32 buffers
+  int lane = 0;            // 1: may run on the side stream, concurrently with the main stream
+  int join = 0;            // 1: the main stream waits for the side stream before this step
   // accounting
   double flops = 0.0;      // algorithmic FP64-or-GEMM flops
   double bytes = 0.0;      // algorithmic bytes
