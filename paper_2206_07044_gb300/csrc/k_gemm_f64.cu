@@ -1,6 +1,6 @@
 // FP64 GEMM on the CUDA cores: C = alpha * A * B for the pairwise
 // contractions (A = T_i as (left x shared), B = T_j as (shared x right)), the
-// R_A L_B core and the projector / absorb products of a compression.
+// R_A L_B core and the Newton-Schulz / preconditioning products of the core SVD.
 //
 // GB300 runs FP64 at 2 DFMA / clock / SM (about 1.2 TFLOP/s for the chip), so
 // these products are FP64-pipe bound at any realistic size; the kernel keeps

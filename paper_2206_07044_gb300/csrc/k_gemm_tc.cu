@@ -1,6 +1,7 @@
 // Reduced-precision GEMM on the 5th-generation tensor cores (tcgen05 + TMEM),
-// fed by TMA: the contraction and absorb products of the mixed forms
-// (TF32 or BF16 inputs, FP32 accumulation; the QR / SVD stay FP64).
+// fed by TMA: the pairwise-contraction products of the mixed forms (TF32,
+// BF16 or split TF32 inputs, FP32 accumulation; QR, SVD and the Q-form absorb
+// stay FP64).
 //
 //   C (m x n, FP64, any strides) = alpha * A (m x k) * B (k x n)
 //

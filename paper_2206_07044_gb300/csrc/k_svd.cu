@@ -5,7 +5,7 @@
 // GB300 runs FP32 58x faster than FP64 (measured 69.7 vs 1.19 TFLOP/s), so the
 // core SVD runs in two precisions:
 //   1. FP32 Jacobi on a float copy of the core, from V = I, until every pair's
-//      relative off-diagonal is below 1e-4 (columns orthogonal to FP32 level);
+//      relative off-diagonal is below 3e-4 (the last sweep leaves ~1e-7);
 //   2. (host schedule) V is re-orthonormalised in FP64 by two Newton-Schulz
 //      steps V <- V (3 I - V^T V) / 2 (from ~1e-5 to below 1e-16) and
 //      G = M V is formed in FP64;
@@ -166,7 +166,7 @@ __device__ __forceinline__ bool jacobi_pair(T* gx, T* gy, T* vx, T* vy, int m, i
   const T s = c * t;
   __syncwarp();
   rot_cols_norms<T, kGlobal>(gx, gy, m, c, s, lane, al, be);
-  rot_cols_g<T, kGlobal>(vx, vy, n, c, s, lane);
+  if (vx) rot_cols_g<T, kGlobal>(vx, vy, n, c, s, lane);
   return rel > p.sig_tol;
 }
 
@@ -181,18 +181,19 @@ __global__ void __launch_bounds__(kThreads) block_jacobi_kernel(JacArgs<T> p) {
   const int nblk = 2 * P;
   const int b = (n + nblk - 1) / nblk;
   T* G = p.G + (int64_t)bidx * p.g_bs;
-  T* V = p.V + (int64_t)bidx * p.v_bs;
+  const bool has_v = (p.V != nullptr);  // without V only G is rotated
+  T* V = has_v ? p.V + (int64_t)bidx * p.v_bs : nullptr;
   int* cnt = p.ws + kWsInts * bidx;
   p.floor2 = p.floor_rel * p.floor_rel * cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Gs = reinterpret_cast<T*>(smem_raw);                  // 2b columns of length m
-  T* Vs = Gs + (size_t)2 * b * m;                          // 2b columns of length n
-  T* nrm = Vs + (size_t)2 * b * n;                         // 2b cached squared norms
+  T* Vs = Gs + (size_t)2 * b * m;                          // 2b columns of length n (if V)
+  T* nrm = Vs + (has_v ? (size_t)2 * b * n : 0);           // 2b cached squared norms
   int* col = reinterpret_cast<int*>(nrm + 2 * b);          // global column of each slot (-1 = pad)
   __shared__ int sig_rot_s;
 
-  if (p.init_v) {
+  if (has_v && p.init_v) {
     for (int c = rank; c < n; c += P)
       for (int r = threadIdx.x; r < n; r += blockDim.x) V[(int64_t)c * n + r] = (r == c) ? T(1) : T(0);
   }
@@ -218,17 +219,19 @@ __global__ void __launch_bounds__(kThreads) block_jacobi_kernel(JacArgs<T> p) {
       for (int s = warp; s < 2 * b; s += nwarps) {
         const int gc = col[s];
         T* gs = Gs + (size_t)s * m;
-        T* vs = Vs + (size_t)s * n;
         T acc = T(0);
         if (gc >= 0) {
           const T* gg = G + (int64_t)gc * m;
-          const T* vv = V + (int64_t)gc * n;
           for (int r = lane; r < m; r += 32) {
             const T x = __ldcg(gg + r);
             gs[r] = x;
             acc = fma(x, x, acc);
           }
-          for (int r = lane; r < n; r += 32) vs[r] = __ldcg(vv + r);
+          if (has_v) {
+            T* vs = Vs + (size_t)s * n;
+            const T* vv = V + (int64_t)gc * n;
+            for (int r = lane; r < n; r += 32) vs[r] = __ldcg(vv + r);
+          }
         }
         acc = warp_sum(acc);
         if (lane == 0) nrm[s] = acc;
@@ -244,8 +247,8 @@ __global__ void __launch_bounds__(kThreads) block_jacobi_kernel(JacArgs<T> p) {
             if (col[x] < 0 || col[y] < 0) continue;
             if (x > y) { int t = x; x = y; y = t; }
             T al = nrm[x], be = nrm[y];
-            if (jacobi_pair(Gs + (size_t)x * m, Gs + (size_t)y * m, Vs + (size_t)x * n, Vs + (size_t)y * n,
-                            m, n, al, be, p, lane))
+            if (jacobi_pair(Gs + (size_t)x * m, Gs + (size_t)y * m, has_v ? Vs + (size_t)x * n : nullptr,
+                            has_v ? Vs + (size_t)y * n : nullptr, m, n, al, be, p, lane))
               sig_rot += (lane == 0);
             if (lane == 0) { nrm[x] = al; nrm[y] = be; }
           }
@@ -258,8 +261,8 @@ __global__ void __launch_bounds__(kThreads) block_jacobi_kernel(JacArgs<T> p) {
             const int x = i, y = b + (i + t) % b;
             if (col[x] < 0 || col[y] < 0) continue;
             T al = nrm[x], be = nrm[y];
-            if (jacobi_pair(Gs + (size_t)x * m, Gs + (size_t)y * m, Vs + (size_t)x * n, Vs + (size_t)y * n,
-                            m, n, al, be, p, lane))
+            if (jacobi_pair(Gs + (size_t)x * m, Gs + (size_t)y * m, has_v ? Vs + (size_t)x * n : nullptr,
+                            has_v ? Vs + (size_t)y * n : nullptr, m, n, al, be, p, lane))
               sig_rot += (lane == 0);
             if (lane == 0) { nrm[x] = al; nrm[y] = be; }
           }
@@ -271,11 +274,13 @@ __global__ void __launch_bounds__(kThreads) block_jacobi_kernel(JacArgs<T> p) {
         const int gc = col[s];
         if (gc < 0) continue;
         T* gg = G + (int64_t)gc * m;
-        T* vv = V + (int64_t)gc * n;
         const T* gs = Gs + (size_t)s * m;
-        const T* vs = Vs + (size_t)s * n;
         for (int r = lane; r < m; r += 32) gg[r] = gs[r];
-        for (int r = lane; r < n; r += 32) vv[r] = vs[r];
+        if (has_v) {
+          T* vv = V + (int64_t)gc * n;
+          const T* vs = Vs + (size_t)s * n;
+          for (int r = lane; r < n; r += 32) vv[r] = vs[r];
+        }
       }
       cl.sync();
     }
@@ -315,12 +320,12 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int m = p.m, n = p.n;
   T* G = p.G + (int64_t)bidx * p.g_bs;
-  T* V = p.V + (int64_t)bidx * p.v_bs;
+  T* V = p.V ? p.V + (int64_t)bidx * p.v_bs : nullptr;
   int* cnt = p.ws + kWsInts * bidx;
   p.floor2 = p.floor_rel * p.floor_rel * cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
   const int np = n + (n & 1);
   const int gw = rank * nwarps + warp, nw = P * nwarps;
-  if (p.init_v) {
+  if (V && p.init_v) {
     for (int c = rank; c < n; c += P)
       for (int r = threadIdx.x; r < n; r += blockDim.x) V[(int64_t)c * n + r] = (r == c) ? T(1) : T(0);
   }
@@ -349,7 +354,8 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
         al = warp_sum(al);
         be = warp_sum(be);
         __syncwarp();
-        if (jacobi_pair<T, true>(gi, gj, V + (int64_t)i * n, V + (int64_t)j * n, m, n, al, be, p, lane))
+        if (jacobi_pair<T, true>(gi, gj, V ? V + (int64_t)i * n : nullptr, V ? V + (int64_t)j * n : nullptr, m, n,
+                                 al, be, p, lane))
           sig_rot += (lane == 0);
       }
       cl.sync();
@@ -377,9 +383,9 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
 }
 
 template <typename T>
-size_t block_smem(int m, int n, int P) {
+size_t block_smem(int m, int n, int P, bool has_v) {
   const int b = (n + 2 * P - 1) / (2 * P);
-  return (size_t)2 * b * (m + n) * sizeof(T) + (size_t)2 * b * (sizeof(T) + sizeof(int)) + 16;
+  return (size_t)2 * b * (m + (has_v ? n : 0)) * sizeof(T) + (size_t)2 * b * (sizeof(T) + sizeof(int)) + 16;
 }
 
 constexpr size_t kSmemCap = 200 * 1024;
@@ -402,7 +408,7 @@ cudaError_t launch_jacobi(const JacArgs<T>& a, int batch, cudaStream_t s) {
       np_set = true;
     }
   }
-  size_t smem = block_smem<T>(a.m, a.n, P);
+  size_t smem = block_smem<T>(a.m, a.n, P, a.V != nullptr);
   const bool use_block = smem <= kSmemCap;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(P, batch, 1);
@@ -429,7 +435,7 @@ cudaError_t launch_jacobi(const JacArgs<T>& a, int batch, cudaStream_t s) {
         P = 8;
         cfg.gridDim = dim3(P, batch, 1);
         attr[0].val.clusterDim.x = P;
-        cfg.dynamicSmemBytes = block_smem<T>(a.m, a.n, P);
+        cfg.dynamicSmemBytes = block_smem<T>(a.m, a.n, P, a.V != nullptr);
         if (cfg.dynamicSmemBytes > kSmemCap) goto fallback;
       }
     }
@@ -451,17 +457,31 @@ fallback:
 // v_i sigma_i^1/2.  Outputs are column-major with leading dimensions ldl / ldr;
 // rows m..ldl-1 (n..ldr-1) are zero-filled so that a Householder product can
 // be applied to them directly.  Ties keep the lower index first.
+//
+// Without V (the polish did not accumulate it), the right factor is recovered
+// afterwards as v_i sigma_i^1/2 = M^T g_i / sigma_i^3/2 by a GEMM: this kernel
+// writes K3[:, p] = g_i / sigma_i^3/2 and only zero-fills rows n..ldr-1 of R.
+// Components with sigma_i <= 1e-13 sigma_max are dropped on both sides there:
+// M^T g_i / sigma_i^3/2 carries an error of eps |M| / sqrt(sigma_i), which
+// must stay small next to the true sqrt(sigma_i).
 __global__ void select_scale_kernel(int m, int n, int k, const double* Gall, int64_t g_bs,
                                     const double* Vall, int64_t v_bs, const double* sigall,
                                     int64_t sig_bs, double* Lall, int64_t l_bs, int ldl, double* Rall,
-                                    int64_t r_bs, int ldr) {
+                                    int64_t r_bs, int ldr, double* K3all, int64_t k3_bs) {
   const int b = blockIdx.x;
   const double* G = Gall + (int64_t)b * g_bs;
-  const double* V = Vall + (int64_t)b * v_bs;
+  const double* V = Vall ? Vall + (int64_t)b * v_bs : nullptr;
   const double* sig = sigall + (int64_t)b * sig_bs;
   double* L = Lall + (int64_t)b * l_bs;
   double* R = Rall + (int64_t)b * r_bs;
+  double* K3 = K3all ? K3all + (int64_t)b * k3_bs : nullptr;
   extern __shared__ int rank_of[];
+  __shared__ double smax;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) mx = fmax(mx, sig[i]);
+    smax = mx;
+  }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double si = sig[i];
     int r = 0;
@@ -478,9 +498,17 @@ __global__ void select_scale_kernel(int m, int n, int k, const double* Gall, int
     if (p >= k) continue;
     const double si = sig[i];
     const double rs = sqrt(si);
-    const double sl = si > 0.0 ? 1.0 / rs : 0.0;
-    for (int r = lane; r < ldl; r += 32) L[(int64_t)p * ldl + r] = r < m ? G[(int64_t)i * m + r] * sl : 0.0;
-    for (int r = lane; r < ldr; r += 32) R[(int64_t)p * ldr + r] = r < n ? V[(int64_t)i * n + r] * rs : 0.0;
+    if (V) {
+      const double sl = si > 0.0 ? 1.0 / rs : 0.0;
+      for (int r = lane; r < ldl; r += 32) L[(int64_t)p * ldl + r] = r < m ? G[(int64_t)i * m + r] * sl : 0.0;
+      for (int r = lane; r < ldr; r += 32) R[(int64_t)p * ldr + r] = r < n ? V[(int64_t)i * n + r] * rs : 0.0;
+    } else {
+      const bool keep = si > 1e-13 * smax && si > 0.0;
+      const double sl = keep ? 1.0 / rs : 0.0, s3 = keep ? 1.0 / (si * rs) : 0.0;
+      for (int r = lane; r < ldl; r += 32) L[(int64_t)p * ldl + r] = r < m ? G[(int64_t)i * m + r] * sl : 0.0;
+      for (int r = lane; r < m; r += 32) K3[(int64_t)p * m + r] = G[(int64_t)i * m + r] * s3;
+      for (int r = n + lane; r < ldr; r += 32) R[(int64_t)p * ldr + r] = 0.0;
+    }
   }
 }
 
@@ -512,29 +540,30 @@ cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64
                            DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr) {
   // a preconditioner: running out of sweeps is not an error (the FP64 stage decides)
   JacArgs<float> a{m, n, G, g_bs, V, v_bs, nullptr, 0, ws, nullptr, 1, 60,
-                   4.0f * (float)m * FLT_EPSILON, 1e-4f, 1e-6f, 0.0f, sweep_ctr};
+                   4.0f * (float)m * FLT_EPSILON, 3e-4f, 1e-6f, 0.0f, sweep_ctr};
   return launch_jacobi(a, batch, s);
 }
 
 cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int64_t v_bs, double* sig,
                            int64_t sig_bs, int* ws, DevState st, int init_v, int batch, cudaStream_t s,
-                           unsigned long long* sweep_ctr) {
+                           unsigned long long* sweep_ctr, double sig_tol) {
   // rotate down to sqrt(m) eps (the cut's subspace error is that over the gap);
   // convergence is judged by the looser sig_tol, so rounding-level rotations
   // never keep the sweep loop alive
   const double rt = sqrt((double)(m > 16 ? m : 16));
   JacArgs<double> a{m, n, G, g_bs, V, v_bs, sig, sig_bs, ws, st.status, init_v, 60,
-                    rt * DBL_EPSILON, 1e-9, 1e-14, 0.0, sweep_ctr};
+                    rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, sweep_ctr};
   return launch_jacobi(a, batch, s);
 }
 
 cudaError_t select_scale_f64(int m, int n, int k, const double* G, int64_t g_bs, const double* V,
                              int64_t v_bs, const double* sig, int64_t sig_bs, double* L, int64_t l_bs,
-                             int ldl, double* R, int64_t r_bs, int ldr, int batch, cudaStream_t s) {
+                             int ldl, double* R, int64_t r_bs, int ldr, int batch, cudaStream_t s,
+                             double* K3, int64_t k3_bs) {
   if (batch <= 0 || k <= 0) return cudaSuccess;
-  if (n > 8192 || ldl < m || ldr < n) return cudaErrorInvalidValue;
+  if (n > 8192 || ldl < m || ldr < n || (!V && !K3)) return cudaErrorInvalidValue;
   select_scale_kernel<<<batch, 256, (size_t)n * sizeof(int), s>>>(m, n, k, G, g_bs, V, v_bs, sig, sig_bs, L,
-                                                                   l_bs, ldl, R, r_bs, ldr);
+                                                                   l_bs, ldl, R, r_bs, ldr, K3, k3_bs);
   return cudaGetLastError();
 }
 

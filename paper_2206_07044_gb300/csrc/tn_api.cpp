@@ -56,7 +56,7 @@ struct CachedPlan {
 };
 
 const char* kFamily[] = {"permute", "gemm_f64", "qr_f64", "jacobi_f64", "select_scale", "rescale",
-                         "finalize", "to_f32", "jacobi_f32", "to_f64", "copy", "apply_q_f64"};
+                         "finalize", "to_f32", "jacobi_f32", "to_f64", "copy", "apply_q_f64", "gemm_tc"};
 constexpr int kNumFamily = tnp::kNumStepKinds;
 
 }  // namespace
@@ -84,6 +84,7 @@ struct tn_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned long long* sweeps = nullptr;  // [2] device: Jacobi sweeps run (FP32, FP64) while profiling
+  int* tc_err = nullptr;                 // device: set by a tensor-core GEMM whose bounded wait ran out
   // profiling
   bool profile = false;
   unsigned long long prof_sweeps[2] = {0, 0};
@@ -320,6 +321,8 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
       return fail(c, TN_ECUDA, "side stream creation failed");
   }
+  if (!c->tc_err && cudaMalloc(&c->tc_err, sizeof(int)) != cudaSuccess) return fail(c, TN_ENOMEM, "error word");
+  cudaMemsetAsync(c->tc_err, 0, sizeof(int), s);
   if (c->profile && !c->sweeps && cudaMalloc(&c->sweeps, 2 * sizeof(unsigned long long)) != cudaSuccess)
     return fail(c, TN_ENOMEM, "profiling counters");
   if (c->profile) cudaMemsetAsync(c->sweeps, 0, 2 * sizeof(unsigned long long), s);
@@ -363,8 +366,9 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
         e = tnk::qr_r_f64(stp.m, stp.n, cview(stp.A), ptr(stp.work), stp.work.bs, wview(stp.C), batch, s);
         break;
       case tnp::ST_JACOBI:
-        e = tnk::jacobi_svd_f64(stp.m, stp.n, ptr(stp.C), stp.C.bs, ptr(stp.aux1), stp.aux1.bs,
-                                ptr(stp.aux2), stp.aux2.bs, c->jac_ws, ds, stp.init_v, batch, s, sw64);
+        e = tnk::jacobi_svd_f64(stp.m, stp.n, ptr(stp.C), stp.C.bs, stp.no_v ? nullptr : ptr(stp.aux1), stp.aux1.bs,
+                                ptr(stp.aux2), stp.aux2.bs, c->jac_ws, ds, stp.init_v, batch, s, sw64,
+                                stp.jac_tol);
         break;
       case tnp::ST_TO_F32:
         e = tnk::convert_f64_to_f32(ptr(stp.src), stp.count, stp.src.bs, reinterpret_cast<float*>(ptr(stp.dst)),
@@ -383,12 +387,18 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
                                     ptr(stp.dst), ptr(stp.out1), stp.dst.bs, batch, s);
         break;
       case tnp::ST_SELECT:
-        e = tnk::select_scale_f64(stp.m, stp.n, stp.k, ptr(stp.C), stp.C.bs, ptr(stp.aux1), stp.aux1.bs,
+        e = tnk::select_scale_f64(stp.m, stp.n, stp.k, ptr(stp.C), stp.C.bs, stp.no_v ? nullptr : ptr(stp.aux1),
+                                  stp.aux1.bs,
                                   ptr(stp.aux2), stp.aux2.bs, ptr(stp.out1), stp.out1.bs, (int)stp.count,
-                                  ptr(stp.out2), stp.out2.bs, stp.init_v, batch, s);
+                                  ptr(stp.out2), stp.out2.bs, stp.init_v, batch, s,
+                                  stp.no_v ? ptr(stp.work) : nullptr, stp.work.bs);
         break;
       case tnp::ST_APPLYQ:
         e = tnk::apply_q_f64(stp.m, stp.n, ptr(stp.work), stp.work.bs, ptr(stp.C), stp.C.bs, stp.k, batch, s);
+        break;
+      case tnp::ST_GEMM_TC:
+        e = tnk::gemm_tc(stp.m, stp.n, stp.k, 1.0, cview(stp.A), cview(stp.B), wview(stp.C), batch, stp.tc_mode,
+                         ptr(stp.work), sizeof(double) * (size_t)stp.work.bs * batch, c->tc_err, s);
         break;
       case tnp::ST_RESCALE:
         e = tnk::rescale_f64(ptr(stp.C), stp.count, stp.C.bs, c->maxbits, ds, batch, s);
@@ -424,12 +434,15 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), c->out_sign, sizeof(int) * batch, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), c->status, sizeof(int) * batch, cudaMemcpyDeviceToHost, s);
   unsigned long long hsw[2] = {0, 0};
+  int htc = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&htc, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && c->profile)
     e = cudaMemcpyAsync(hsw, c->sweeps, sizeof(hsw), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
   c->prof_sweeps[0] += hsw[0];
   c->prof_sweeps[1] += hsw[1];
+  if (htc) return fail(c, TN_ETIMEOUT, "a tensor-core GEMM's bounded wait ran out");
   for (size_t q = 0; q < evs.size(); ++q) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, evs[q].first, evs[q].second);
@@ -490,6 +503,7 @@ void tn_destroy(tn_ctx* c) {
   cudaFree(c->out_log);
   cudaFree(c->out_sign);
   cudaFree(c->sweeps);
+  cudaFree(c->tc_err);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -619,7 +633,7 @@ int tn_contract_approx(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int 
                        int* sign_out) {
   if (!c || !inst_ids || !logabsz_out || !sign_out || n_inst < 1) return fail(c, TN_EINVAL, "bad arguments");
   if (chi < 1) return fail(c, TN_EINVAL, "chi must be >= 1");
-  if (prec != TN_F64) return fail(c, TN_EINVAL, "precision form not available in this build");
+  if (prec < TN_F64 || prec > TN_TF32X3) return fail(c, TN_EINVAL, "unknown precision form");
   for (int q = 0; q < n_inst; ++q)
     if (inst_ids[q] < 0 || inst_ids[q] >= (int)c->insts.size()) return fail(c, TN_EINVAL, "unknown instance id");
   DeviceGuard g(c->device);
@@ -654,7 +668,7 @@ int tn_debug_tensor(tn_ctx* c, int n_inst, const int* inst_ids, int which, int c
   if (!c || !inst_ids || !ndim_out || n_inst < 1 || which < 0 || which >= n_inst)
     return fail(c, TN_EINVAL, "bad arguments");
   if (chi < 1) return fail(c, TN_EINVAL, "chi must be >= 1");
-  if (prec != TN_F64) return fail(c, TN_EINVAL, "precision form not available in this build");
+  if (prec < TN_F64 || prec > TN_TF32X3) return fail(c, TN_EINVAL, "unknown precision form");
   for (int q = 0; q < n_inst; ++q) {
     if (inst_ids[q] < 0 || inst_ids[q] >= (int)c->insts.size()) return fail(c, TN_EINVAL, "unknown instance id");
     if (!same_group(c, inst_ids[0], inst_ids[q])) return fail(c, TN_EINVAL, "instances do not share a tree and structure");
@@ -707,7 +721,9 @@ int tn_plan_stats_get(tn_ctx* c, int inst_id, int chi, int prec, tn_plan_stats* 
   out->peak_bytes = 8.0 * (double)p->arena_units;
   int64_t launches = 0;
   for (auto& s : p->steps)  // rescale = max + scale kernels; copies are not kernels
-    launches += (s.kind == tnp::ST_RESCALE) ? 2 : (s.kind == tnp::ST_COPY ? 0 : 1);
+    launches += (s.kind == tnp::ST_RESCALE || s.kind == tnp::ST_JACOBI32 || s.kind == tnp::ST_JACOBI)
+                    ? (s.kind == tnp::ST_RESCALE ? 2 : 1)
+                    : (s.kind == tnp::ST_COPY ? 0 : (s.kind == tnp::ST_GEMM_TC ? 3 : 1));  // TC: 2 staging + GEMM
   out->kernel_launches = launches;
   return TN_OK;
 }

@@ -48,7 +48,8 @@ cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW 
 // sweep_ctr (optional, device): the sweeps run are added to it.
 cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int64_t v_bs,
                            double* sig, int64_t sig_bs, int* ws, DevState st, int init_v,
-                           int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr);
+                           int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr,
+                           double sig_tol = 1e-8);
 // The FP32 preconditioning pass (V = I first); never sets a status.
 cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64_t v_bs, int* ws,
                            DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr);
@@ -61,10 +62,14 @@ cudaError_t convert_f32_to_f64(const float* x, int64_t n, int64_t xbs, double* y
 // After Jacobi: pick the k largest sigma and write the truncated factors
 // with sigma^1/2 absorbed: L[:, p] = g_i / sqrt(sigma_i) (= u_i sqrt(sigma_i)),
 // R[:, p] = V[:, i] sqrt(sigma_i); column-major with leading dims ldl >= m,
-// ldr >= n, rows beyond m (n) zero-filled.
+// ldr >= n, rows beyond m (n) zero-filled.  With V == nullptr, R's rows
+// 0..n-1 are left for a GEMM R = G0^T K3 (G0 the Jacobi input) and K3
+// (m x k column-major) receives g_i / sigma_i^3/2, zero for sigma_i <=
+// 1e-13 sigma_max (those columns of L are zero too).
 cudaError_t select_scale_f64(int m, int n, int k, const double* G, int64_t g_bs, const double* V,
                              int64_t v_bs, const double* sig, int64_t sig_bs, double* L, int64_t l_bs,
-                             int ldl, double* R, int64_t r_bs, int ldr, int batch, cudaStream_t s);
+                             int ldl, double* R, int64_t r_bs, int ldr, int batch, cudaStream_t s,
+                             double* K3 = nullptr, int64_t k3_bs = 0);
 
 // X[b] <- Q[b] X[b], Q the Householder product a qr_r_f64 call left in `work`
 // (same m, n, work, work_bs and batch).  X: m x k column-major (ld m).

@@ -165,13 +165,14 @@ extern "C" int tn_contract_approx_noalloc(const tn_network_desc* net, const tn_t
         ce = tnk::qr_r_f64(stp.m, stp.n, cview(stp.A), ptr(stp.work), stp.work.bs, wview(stp.C), batch, s);
         break;
       case tnp::ST_JACOBI:
-        ce = tnk::jacobi_svd_f64(stp.m, stp.n, ptr(stp.C), stp.C.bs, ptr(stp.aux1), stp.aux1.bs, ptr(stp.aux2),
+        ce = tnk::jacobi_svd_f64(stp.m, stp.n, ptr(stp.C), stp.C.bs, stp.no_v ? nullptr : ptr(stp.aux1), stp.aux1.bs, ptr(stp.aux2),
                                  stp.aux2.bs, jac_ws, ds, stp.init_v, batch, s);
         break;
       case tnp::ST_SELECT:
-        ce = tnk::select_scale_f64(stp.m, stp.n, stp.k, ptr(stp.C), stp.C.bs, ptr(stp.aux1), stp.aux1.bs,
+        ce = tnk::select_scale_f64(stp.m, stp.n, stp.k, ptr(stp.C), stp.C.bs, stp.no_v ? nullptr : ptr(stp.aux1), stp.aux1.bs,
                                    ptr(stp.aux2), stp.aux2.bs, ptr(stp.out1), stp.out1.bs, (int)stp.count,
-                                   ptr(stp.out2), stp.out2.bs, stp.init_v, batch, s);
+                                   ptr(stp.out2), stp.out2.bs, stp.init_v, batch, s,
+                                   stp.no_v ? ptr(stp.work) : nullptr, stp.work.bs);
         break;
       case tnp::ST_APPLYQ:
         ce = tnk::apply_q_f64(stp.m, stp.n, ptr(stp.work), stp.work.bs, ptr(stp.C), stp.C.bs, stp.k, batch, s);

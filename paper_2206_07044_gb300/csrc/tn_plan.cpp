@@ -20,6 +20,8 @@
 // (R_A = A, i.e. Q_A = 1); likewise for B.
 #include "tn_plan.h"
 
+#include "tn_kernels.h"
+
 #include <algorithm>
 #include <map>
 #include <unordered_map>
@@ -198,6 +200,29 @@ struct Builder {
     plan->gemm_flops += st.flops;
     add(st);
   }
+  bool mixed() const { return plan->prec != 0; }
+  int tc_mode() const { return plan->prec == 1 ? 0 : (plan->prec == 2 ? 1 : 2); }
+  // C = A B on the tensor cores; the staged-operand scratch is a temporary
+  void gemm_tc_step(int m, int n, int k, PView A, PView B, PView C, bool count_flops) {
+    Step st;
+    st.kind = ST_GEMM_TC;
+    st.tc_mode = tc_mode();
+    st.m = m;
+    st.n = n;
+    st.k = k;
+    st.A = A;
+    st.B = B;
+    st.C = C;
+    // per-instance share of the batch's staged operands (+ slack for the 256-byte roundings)
+    const int64_t per = (int64_t)tnk::gemm_tc_workspace_bytes(m, n, k, st.tc_mode, 1) + 1024;
+    int64_t off;
+    st.work = temp((per + 7) / 8, &off);
+    st.flops = count_flops ? 2.0 * m * n * (double)k : 0.0;
+    st.bytes = 8.0 * ((double)m * k + (double)k * n + (double)m * n);
+    plan->gemm_flops += st.flops;
+    add(st);
+    arena.release(off, (per + 7) / 8);
+  }
   void rescale(int vi) {
     Step st;
     st.kind = ST_RESCALE;
@@ -274,7 +299,10 @@ struct Builder {
     PView C = base_view(vals[ic]);
     C.rs = n;
     C.cs = 1;
-    gemm((int)m, (int)n, (int)kk, A, B, C);
+    if (mixed())
+      gemm_tc_step((int)m, (int)n, (int)kk, A, B, C, true);
+    else
+      gemm((int)m, (int)n, (int)kk, A, B, C);
     rescale(ic);
     for (int t : tmps) release_value(t);
     release_value(ia0);
@@ -449,6 +477,8 @@ struct Builder {
       st.aux1 = V;
       st.aux2 = sig;
       st.init_v = 0;
+      st.no_v = 1;   // V_k is recovered after the sweeps from M^T U_k (a GEMM), see below
+      st.jac_tol = 1e-8;
       st.flops = svd_flops((double)rA, (double)rB);
       st.bytes = 8.0 * (2.0 * Jm * Jn + 2.0 * Jn * Jn);
       plan->svd_flops += st.flops;
@@ -461,44 +491,61 @@ struct Builder {
     // and the Householder products of the two QRs are applied in place.
     const int nbond = (int)dim.size();
     dim.push_back(kk);
-    std::vector<int> bi = {nbond};
-    bi.insert(bi.end(), sp.rem_i.begin(), sp.rem_i.end());
-    std::vector<int> bj = {nbond};
-    bj.insert(bj.end(), sp.rem_j.begin(), sp.rem_j.end());
-    int na = new_arena_value(bi);
-    int nbv = new_arena_value(bj);
-    PView Ab = base_view(vals[na]), Bb = base_view(vals[nbv]);
+    int na = -1, nbv = -1;
     {
-      Step st;
-      st.kind = ST_SELECT;
-      st.m = (int)Jm;
-      st.n = (int)Jn;
-      st.k = (int)kk;
-      st.C = G;
-      st.aux1 = V;
-      st.aux2 = sig;
-      // left singular side (rows of the Jacobi matrix) and right side
-      st.out1 = tall ? Ab : Bb;
-      st.out2 = tall ? Bb : Ab;
-      st.count = tall ? DA : DB;     // leading dimension of out1
-      st.init_v = (int)(tall ? DB : DA);  // leading dimension of out2
-      st.bytes = 8.0 * (double)kk * (Jm + Jn + DA + DB);
-      add(st);
+      std::vector<int> bi = {nbond};
+      bi.insert(bi.end(), sp.rem_i.begin(), sp.rem_i.end());
+      std::vector<int> bj = {nbond};
+      bj.insert(bj.end(), sp.rem_j.begin(), sp.rem_j.end());
+      na = new_arena_value(bi);
+      nbv = new_arena_value(bj);
+      PView Ab = base_view(vals[na]), Bb = base_view(vals[nbv]);
+      PView K3 = tmp(Jm * kk);
+      {
+        Step st;
+        st.kind = ST_SELECT;
+        st.m = (int)Jm;
+        st.n = (int)Jn;
+        st.k = (int)kk;
+        st.C = G;
+        st.aux1 = V;
+        st.aux2 = sig;
+        st.no_v = 1;
+        st.work = K3;
+        // left singular side (rows of the Jacobi matrix) and right side
+        st.out1 = tall ? Ab : Bb;
+        st.out2 = tall ? Bb : Ab;
+        st.count = tall ? DA : DB;     // leading dimension of out1
+        st.init_v = (int)(tall ? DB : DA);  // leading dimension of out2
+        st.bytes = 8.0 * (double)kk * (Jm + Jn + DA + DB);
+        add(st);
+      }
+      // right factor V_k sigma^1/2 = G0^T U_k sigma^-1/2 = G0^T K3 into rows 0..Jn-1 of out2
+      {
+        PView G0T = M0c, K3v = K3, R = tall ? Bb : Ab;
+        G0T.rs = Jm;
+        G0T.cs = 1;
+        K3v.rs = 1;
+        K3v.cs = Jm;
+        R.rs = 1;
+        R.cs = tall ? DB : DA;
+        gemm((int)Jn, (int)kk, (int)Jm, G0T, K3v, R, 1.0, 0.0, true);
+      }
+      auto apply = [&](int64_t mm, const PView& work, const PView& X) {
+        Step st;
+        st.kind = ST_APPLYQ;
+        st.m = (int)mm;
+        st.n = (int)dab;
+        st.k = (int)kk;
+        st.work = work;
+        st.C = X;
+        st.flops = 0.0;
+        st.bytes = 8.0 * (mm * dab + 2.0 * mm * kk);
+        add(st);
+      };
+      if (DA > dab) apply(DA, workA, Ab);
+      if (DB > dab) apply(DB, workB, Bb);
     }
-    auto apply = [&](int64_t mm, const PView& work, const PView& X) {
-      Step st;
-      st.kind = ST_APPLYQ;
-      st.m = (int)mm;
-      st.n = (int)dab;
-      st.k = (int)kk;
-      st.work = work;
-      st.C = X;
-      st.flops = 0.0;
-      st.bytes = 8.0 * (mm * dab + 2.0 * mm * kk);
-      add(st);
-    };
-    if (DA > dab) apply(DA, workA, Ab);
-    if (DB > dab) apply(DB, workB, Bb);
     // the paper's absorb contractions: (D_A x r_A)(r_A x k) and (k x r_B)(r_B x D_B)
     plan->gemm_flops += 2.0 * DA * rA * (double)kk + 2.0 * kk * rB * (double)DB;
     rescale(na);

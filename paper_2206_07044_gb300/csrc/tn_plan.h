@@ -35,8 +35,9 @@ enum StepKind : int {
   ST_TO_F64 = 9,      // src (FP32) -> dst and out1 (FP64), count elements
   ST_COPY = 10,       // dst <- src, count elements per instance (same per-instance stride)
   ST_APPLYQ = 11,     // C (m x k col-major) <- Q C, Q the reflectors in `work` (m x n QR)
+  ST_GEMM_TC = 12,    // C = alpha A B on tcgen05 tensor cores (tc_mode), FP64 in and out, `work` scratch
 };
-constexpr int kNumStepKinds = 12;
+constexpr int kNumStepKinds = 13;
 
 struct Step {
   int kind = 0;
@@ -55,6 +56,10 @@ struct Step {
   double alpha = 1.0, beta = 0.0;  // gemm: C = alpha A B + beta C
   int init_v = 1;          // jacobi: start from V = I
   int64_t fbs_src = 0, fbs_dst = 0;  // per-instance strides in floats for FP32 buffers
+  int tc_mode = 0;         // tensor-core GEMM: 0 TF32, 1 BF16, 2 split TF32
+  int64_t work_bytes = 0;  // tensor-core GEMM: scratch bytes for the whole batch (per instance x batch)
+  double jac_tol = 1e-9;   // FP64 Jacobi: relative off-diagonal below which a pair counts as converged
+  int no_v = 0;            // FP64 Jacobi / select: V not accumulated; select writes K3 into `work`
   int lane = 0;            // 1: may run on the side stream, concurrently with the main stream
   int join = 0;            // 1: the main stream waits for the side stream before this step
   // accounting
