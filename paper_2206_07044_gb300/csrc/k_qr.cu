@@ -14,6 +14,7 @@
 // matrix over P SMs is what sets the speed.
 #include <cooperative_groups.h>
 
+#include "tn_cluster.h"
 #include "tn_kernels.h"
 
 namespace cg = cooperative_groups;
@@ -208,15 +209,20 @@ namespace {
 
 constexpr size_t kQrSmemCap = 210 * 1024;
 
+void ensure_qr_attrs() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemCap);
+  cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kVSmem * (int)sizeof(double));
+  cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  done = true;
+}
+
 template <bool kSmem>
 cudaError_t launch_qr(int P, int m, int n, View A, double* work, int64_t work_bs, double* taus, ViewW R,
                       int batch, cudaStream_t s, size_t smem) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(qr_cluster_kernel<kSmem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemCap);
-    cudaFuncSetAttribute(qr_cluster_kernel<kSmem>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    attr_done = true;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(P, batch, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
@@ -229,14 +235,6 @@ cudaError_t launch_qr(int P, int m, int n, View A, double* work, int64_t work_bs
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (P > 8) {
-    // a 16-CTA cluster must fit in one GPC; fall back to 8 when it cannot be placed
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, qr_cluster_kernel<kSmem>, &cfg) != cudaSuccess || nclusters < 1) {
-      cudaGetLastError();
-      return cudaErrorNotSupported;
-    }
-  }
   return cudaLaunchKernelEx(&cfg, qr_cluster_kernel<kSmem>, m, n, A, work, work_bs, taus, R);
 }
 
@@ -246,24 +244,29 @@ cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW 
                      cudaStream_t s) {
   if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
   if (batch > 65535) return cudaErrorInvalidValue;
+  ensure_qr_attrs();
   // tau scratch sits after the batch of working copies
   double* taus = work + (int64_t)batch * work_bs;
-  // cluster size: about 16 columns per CTA, up to 16 CTAs (non-portable size)
-  int P = (n + 15) / 16;
-  if (P > 16) P = 16;
-  if (P < 1) P = 1;
-  for (; P >= 1; P = (P > 8 ? 8 : P)) {
-    const int nc = (n + P - 1) / P;
-    const size_t smem_cols = ((size_t)nc * m + (size_t)m) * sizeof(double);
-    cudaError_t e;
-    if (smem_cols <= kQrSmemCap)
-      e = launch_qr<true>(P, m, n, A, work, work_bs, taus, R, batch, s, smem_cols);
-    else
-      e = launch_qr<false>(P, m, n, A, work, work_bs, taus, R, batch, s,
-                           (m <= kVSmem) ? (size_t)m * sizeof(double) : 0);
-    if (e != cudaErrorNotSupported || P <= 8) return e;
-  }
-  return cudaErrorInvalidValue;
+  // cluster size: at least ~16 columns per CTA and at most 16 CTAs (non-portable
+  // size); within [pmax/2, pmax] the size with the fewest waves per CTA of work
+  int pmax = (n + 15) / 16;
+  if (pmax > 16) pmax = 16;
+  if (pmax < 1) pmax = 1;
+  const int pmin = pmax / 2 > 0 ? pmax / 2 : 1;
+  auto smem_cols = [&](int q) {
+    const int nc = (n + q - 1) / q;
+    const size_t b = ((size_t)nc * m + (size_t)m) * sizeof(double);
+    return b <= kQrSmemCap ? b : (size_t)-1;
+  };
+  auto even = [](int) { return 1.0; };
+  int P = choose_cluster((const void*)qr_cluster_kernel<true>, kThreads, batch, pmin, pmax, smem_cols, even);
+  if (P > 0) return launch_qr<true>(P, m, n, A, work, work_bs, taus, R, batch, s, smem_cols(P));
+  // columns do not fit in shared memory: update them in global memory
+  const size_t gsm = (m <= kVSmem) ? (size_t)m * sizeof(double) : 0;
+  P = choose_cluster((const void*)qr_cluster_kernel<false>, kThreads, batch, pmin, pmax, [&](int) { return gsm; },
+                     even);
+  if (P < 1) P = pmax < 8 ? pmax : 8;
+  return launch_qr<false>(P, m, n, A, work, work_bs, taus, R, batch, s, gsm);
 }
 
 }  // namespace tnk

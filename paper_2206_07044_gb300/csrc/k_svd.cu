@@ -36,6 +36,7 @@
 
 #include <cfloat>
 
+#include "tn_cluster.h"
 #include "tn_kernels.h"
 
 namespace cg = cooperative_groups;
@@ -396,52 +397,47 @@ cudaError_t launch_jacobi(const JacArgs<T>& a, int batch, cudaStream_t s) {
   if (a.m < a.n || batch > 65535) return cudaErrorInvalidValue;
   cudaError_t ze = cudaMemsetAsync(a.ws, 0, sizeof(int) * kWsInts * (size_t)batch, s);
   if (ze != cudaSuccess) return ze;
-  // cluster size: about one block pair of >= 8 columns per CTA, up to 16 CTAs
-  // (non-portable; falls back to 8 when a 16-CTA cluster cannot be placed)
-  int P = a.n / 16;
-  if (P > 16) P = 16;
-  if (P < 1) P = 1;
-  if (P > 8) {
-    static bool np_set = false;
-    if (!np_set) {
-      cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      np_set = true;
-    }
+  // cluster size: at most one block pair of 8 columns per CTA and 16 CTAs
+  // (non-portable size); within [pmax/2, pmax] the size with the fewest
+  // waves per CTA of work for this batch
+  int pmax = a.n / 16;
+  if (pmax > 16) pmax = 16;
+  if (pmax < 1) pmax = 1;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    attr_set = true;
   }
-  size_t smem = block_smem<T>(a.m, a.n, P, a.V != nullptr);
-  const bool use_block = smem <= kSmemCap;
+  const bool has_v = a.V != nullptr;
+  auto smem_of = [&](int q) {
+    const size_t sm = block_smem<T>(a.m, a.n, q, has_v);
+    return sm <= kSmemCap ? sm : (size_t)-1;
+  };
+  // a round pairs b = n / 2P columns with b others: b pairs per inner round over 8 warps
+  auto imbalance = [&](int q) {
+    const int b = (a.n + 2 * q - 1) / (2 * q);
+    const int nw = kThreads / 32;
+    return (double)((b + nw - 1) / nw * nw) / b;
+  };
+  int P = choose_cluster((const void*)block_jacobi_kernel<T>, kThreads, batch, pmax / 2 > 0 ? pmax / 2 : 1, pmax,
+                         smem_of, imbalance);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(P, batch, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = P;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (use_block) {
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
-      attr_set = true;
-    }
-    cfg.dynamicSmemBytes = smem;
-    if (P > 8) {
-      int nclusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&nclusters, block_jacobi_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
-        cudaGetLastError();
-        P = 8;
-        cfg.gridDim = dim3(P, batch, 1);
-        attr[0].val.clusterDim.x = P;
-        cfg.dynamicSmemBytes = block_smem<T>(a.m, a.n, P, a.V != nullptr);
-        if (cfg.dynamicSmemBytes > kSmemCap) goto fallback;
-      }
-    }
+  if (P > 0) {
+    cfg.gridDim = dim3(P, batch, 1);
+    attr[0].val.clusterDim.x = P;
+    cfg.dynamicSmemBytes = smem_of(P);
     return cudaLaunchKernelEx(&cfg, block_jacobi_kernel<T>, a);
   }
-fallback:
+  // block pairs do not fit in shared memory: column pairs from global memory
   P = a.n / 64;
   if (P > 8) P = 8;
   if (P < 1) P = 1;
