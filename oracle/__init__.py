@@ -15,8 +15,10 @@ Modules:
   exact   -- independent references: brute-force sums over spin / edge
              configurations, row transfer matrices, closed forms, perfect
              matching counts, and full einsum contraction of tiny networks.
-  grad    -- d log|Z| / d T by reverse-mode differentiation of the same
-             executor written in plain PyTorch CPU float64 ops.
+  grad    -- d log|Z| / d T_v: the same schedule re-run with its operands
+             kept, then walked backwards (matrix-product adjoints, the exact
+             power-of-two rescale, and the adjoint of the truncated SVD of
+             X = A B for each compression), in plain numpy FP64.
 
 Every function states the passage of the paper it follows.  Where the paper
 is silent the reading used is stated in the docstring.
