@@ -218,6 +218,48 @@ def oracle_sample(rows: int = 8, cores: int | None = None):
 
 
 # ---------------------------------------------------------------------------
+# GEMM forms on a smaller calibration batch
+
+CAL_L, CAL_INSTANCES = 16, 4
+
+
+def calibrate_forms(ctx, torch):
+    """Throughput and log|Z| error of each GEMM form against the FP64 form.
+
+    Runs a 16x16 open lattice (D=4, Normal(0.2,1), boundary-row tree, chi=64;
+    the same shapes per compression as the full workload) as one batch per form,
+    and the FP64 form once more with one instance per call.  The error is the
+    largest |ln|Z|_form - ln|Z|_f64| / |ln|Z|_f64| over the batch; a form meets the
+    metric's gate at 1e-6.
+    """
+    from tn_inputs import networks as nw
+    from tn_inputs import trees as tr
+    n, edges = nw.square_lattice(CAL_L, CAL_L)
+    tree = tr.boundary_rows(CAL_L, CAL_L)
+    ids = []
+    for s in range(CAL_INSTANCES):
+        nid = ctx.load_network(nw.random_network(n, edges, D, seed=1000 + s))
+        ids.append(ctx.load_tree(nid, tree))
+    out = {"workload": f"{CAL_L}x{CAL_L} open square lattice, D={D}, Normal(0.2,1), {CAL_INSTANCES} seeds, "
+                       f"boundary-row tree, chi={CHI}", "gate_rel_err": 1e-6}
+    ref = None
+    for prec in ("f64", "tf32x3", "tf32", "bf16"):
+        ctx.contract(ids, CHI, prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lz, _ = ctx.contract(ids, CHI, prec)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ref is None:
+            ref = lz
+        err = float(max(abs(a - b) / abs(b) for a, b in zip(lz, ref)))
+        out[prec] = {"evals_per_s": CAL_INSTANCES / dt, "rel_err_vs_f64": err, "meets_gate": bool(err <= 1e-6)}
+    t0 = time.perf_counter()
+    for i in ids:
+        ctx.contract([i], CHI, "f64")
+    torch.cuda.synchronize()
+    out["f64_unbatched"] = {"evals_per_s": CAL_INSTANCES / (time.perf_counter() - t0)}
+    return out
 
 
 def run_ours(args):
@@ -245,10 +287,11 @@ def run_ours(args):
     def step():
         return ctx.contract(ids, CHI, args.prec)
 
+    # warm-up: the first pass runs eagerly, the second captures the schedule as a
+    # CUDA graph, later passes replay it
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    ctx.profile(True)
     barrier(device)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -260,9 +303,19 @@ def run_ours(args):
         torch.cuda.synchronize()
     barrier(device)
     ms = e0.elapsed_time(e1) / args.steps
+    graph = ctx.graph_info()
+    ms_max = max_over_ranks(ms, device)
+    # per-kernel device times: one more pass with events around every launch
+    # (eager launches, one stream), after the timed region
+    ctx.profile(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = p0.elapsed_time(p1)
     fam = ctx.kernel_times()
     ctx.profile(False)
-    ms_max = max_over_ranks(ms, device)
     value = world * INSTANCES / (ms_max / 1e3)
 
     # end to end: pinned host inputs -> device, contraction, results -> host, every step
@@ -279,13 +332,26 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, device)
 
+    # the plain FP64 form: the same contraction, one instance per call (no batching)
+    plain = None
+    if rank == 0 and not args.no_forms:
+        ctx.contract(ids[:1], CHI, "f64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.contract(ids[:1], CHI, "f64")
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t0
+        plain = {"value": 1.0 / plain_s, "unit": UNIT, "ms_per_eval": plain_s * 1e3,
+                 "how": "one instance per tn_contract_approx call, FP64, same workload"}
+    forms = calibrate_forms(ctx, torch) if rank == 0 and not args.no_forms else None
+
     if rank != 0:
         return
     # roofline of the dominant kernel family (device time share inside the timed region)
     fam_sorted = sorted(fam, key=lambda r: -r[2])
     top = fam_sorted[0]
     algo = {"jacobi_f64": stats["svd_flops"], "qr_f64": stats["qr_flops"], "gemm_f64": stats["gemm_flops"]}
-    launches_per_step = {name: nl / args.steps for name, nl, _ in fam}
+    launches_per_step = {name: nl for name, nl, _ in fam}
     name, nl, tot_ms = top
     avg_ms = tot_ms / nl
     roof = None
@@ -295,7 +361,8 @@ def run_ours(args):
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (unit counts and clock)",
-                "share_of_step": tot_ms / (ms * args.steps)}
+                "share_of_step": tot_ms / prof_ms,
+                "timing": "CUDA events around each launch of one profiled pass (eager, one stream)"}
     gflop_step = (stats["gemm_flops"] + stats["qr_flops"] + stats["svd_flops"]) * INSTANCES * world / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -308,8 +375,13 @@ def run_ours(args):
         "e2e": {"value": world * INSTANCES / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(stats["kernel_launches"]) * args.steps,
+        "plain_fp64_unbatched": plain,
+        "vs_plain_fp64_unbatched": (value / world) / plain["value"] if plain else None,
+        "forms": forms,
         "roofline": roof,
-        "kernel_share": {n_: round(t_ / (ms * args.steps), 4) for n_, _, t_ in fam_sorted},
+        "kernel_share": {n_: round(t_ / prof_ms, 4) for n_, _, t_ in fam_sorted},
+        "profiled_pass_ms": prof_ms,
+        "graph": graph,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -347,6 +419,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f64", choices=["f64", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the unbatched and mixed-form legs")
     ap.add_argument("--L", type=int, default=L, help="lattice side (a smaller case for profiling)")
     ap.add_argument("--instances", type=int, default=INSTANCES, help="instances per GPU")
     args = ap.parse_args()

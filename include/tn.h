@@ -114,6 +114,22 @@ void tn_destroy(tn_ctx* ctx);
  * default stream).  The stream must belong to the context's device. */
 int tn_set_stream(tn_ctx* ctx, void* cuda_stream);
 
+/* CUDA-graph replay of whole schedules (batching across instances, Algorithm 1
+ * run as one pre-built launch sequence).  mode 1 (default): the first
+ * tn_contract_approx on a given (plan, ordered instance list) runs eagerly, the
+ * second captures the whole pass (input gather, every kernel and copy of the
+ * schedule, both streams) into a graph and launches it, later calls replay it.
+ * Results are bitwise identical to eager launches.  A capture the runtime
+ * refuses leaves that key on eager launches (counted in `refused`).  Graphs
+ * are dropped when the context's device buffers grow.  mode 0: always eager.
+ * Profiling (tn_profile_enable) and tn_debug_tensor always run eagerly.
+ * Errors: TN_EINVAL for another mode. */
+int tn_set_graph_mode(tn_ctx* ctx, int mode);
+
+/* Counters of the graph path since tn_create: graphs captured, replays
+ * launched, captures refused.  Any pointer may be NULL. */
+int tn_graph_info(const tn_ctx* ctx, int64_t* captured, int64_t* replays, int64_t* refused);
+
 /* Copy a network into the context (host data -> device).  Validates that each
  * bond appears in exactly two tensors and that entries are finite
  * (TN_ENONFINITE otherwise).  *net_id receives the network's id. */

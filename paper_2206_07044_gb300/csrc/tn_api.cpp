@@ -55,6 +55,19 @@ struct CachedPlan {
   tnp::Plan plan;
 };
 
+// A captured schedule: one plan, one ordered member list, one set of device buffers.
+struct GraphKey {
+  uint64_t plan_serial, buf_gen;
+  std::vector<int> members;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(plan_serial, buf_gen, members) < std::tie(o.plan_serial, o.buf_gen, o.members);
+  }
+};
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  bool failed = false;  // capture was refused: this key always runs eagerly
+};
+
 const char* kFamily[] = {"permute", "gemm_f64", "qr_f64", "jacobi_f64", "select_scale", "rescale",
                          "finalize", "to_f32", "jacobi_f32", "to_f64", "copy", "apply_q_f64", "gemm_tc"};
 constexpr int kNumFamily = tnp::kNumStepKinds;
@@ -85,6 +98,14 @@ struct tn_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned long long* sweeps = nullptr;  // [2] device: Jacobi sweeps run (FP32, FP64) while profiling
   int* tc_err = nullptr;                 // device: set by a tensor-core GEMM whose bounded wait ran out
+  // CUDA graphs: a schedule runs eagerly on its first call (warming every launch
+  // configuration), is captured on the second and replayed from then on
+  int graph_mode = 1;
+  uint64_t plan_serial = 0;
+  uint64_t buf_gen = 0;  // bumped whenever a buffer a captured graph points into moves
+  cudaStream_t cap = nullptr;
+  std::map<GraphKey, GraphRec> graphs;
+  int64_t graph_captured = 0, graph_replays = 0, graph_refused = 0;
   // profiling
   bool profile = false;
   unsigned long long prof_sweeps[2] = {0, 0};
@@ -284,8 +305,51 @@ const tnp::Plan* get_plan(tn_ctx* c, int inst, int chi, int prec, int* rc) {
     *rc = fail(c, TN_EFORMAT, "plan: " + err);
     return nullptr;
   }
+  cp.plan.serial = ++c->plan_serial;
   auto res = c->plans.insert_or_assign(key, std::move(cp));
   return &res.first->second.plan;
+}
+
+// Forget every captured graph (a buffer they point into has moved).
+void drop_graphs(tn_ctx* c) {
+  for (auto& g : c->graphs)
+    if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+  c->graphs.clear();
+  ++c->buf_gen;
+}
+
+// Capture one pass of `enqueue` on the context's capture stream and
+// instantiate it.  On any refusal the key is marked failed and keeps running
+// eagerly (the same kernels, launched one by one).
+template <typename F>
+void capture_graph(tn_ctx* c, GraphRec* gr, F& enqueue) {
+  gr->failed = true;
+  if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ++c->graph_refused;
+    return;
+  }
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    ++c->graph_refused;
+    return;
+  }
+  const std::string saved = c->err;
+  const int rc = enqueue(c->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  c->err = saved;
+  cudaGraphExec_t ex = nullptr;
+  if (rc == TN_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&ex, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (rc != TN_OK || e != cudaSuccess || !ex) {
+    cudaGetLastError();
+    ++c->graph_refused;
+    return;
+  }
+  gr->exec = ex;
+  gr->failed = false;
+  ++c->graph_captured;
 }
 
 // Run the plan on a batch.  With stop_op >= 0, only the steps of tree ops
@@ -297,6 +361,7 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   if (batch > 65535) return fail(c, TN_EINVAL, "more than 65535 instances in one batch");
   const tnp::Structure& st = c->nets[c->insts[members[0]].net].st;
   cudaError_t e;
+  const void* before[3] = {c->arena, c->inbuf, c->expo};
   const size_t arena_need = sizeof(double) * (size_t)std::max<int64_t>(plan.arena_units, 1) * batch;
   if ((e = ensure(&c->arena, &c->arena_bytes, arena_need)) != cudaSuccess)
     return fail(c, TN_ENOMEM, "arena allocation of " + std::to_string(arena_need) + " bytes failed");
@@ -305,16 +370,6 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
     return fail(c, TN_ENOMEM, "input buffer allocation failed");
   int rc = ensure_scratch(c, batch);
   if (rc != TN_OK) return rc;
-  cudaStream_t s = c->stream;
-  for (int b = 0; b < batch; ++b) {
-    const NetRec& nr = c->nets[c->insts[members[b]].net];
-    e = cudaMemcpyAsync(c->inbuf + (size_t)b * st.in_total, nr.d_data, sizeof(double) * st.in_total,
-                        cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "gather inputs");
-  }
-  cudaMemsetAsync(c->expo, 0, sizeof(long long) * batch, s);
-  cudaMemsetAsync(c->status, 0, sizeof(int) * batch, s);
-  tnk::DevState ds{c->expo, c->status};
   if (!c->side) {
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -322,10 +377,10 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
       return fail(c, TN_ECUDA, "side stream creation failed");
   }
   if (!c->tc_err && cudaMalloc(&c->tc_err, sizeof(int)) != cudaSuccess) return fail(c, TN_ENOMEM, "error word");
-  cudaMemsetAsync(c->tc_err, 0, sizeof(int), s);
   if (c->profile && !c->sweeps && cudaMalloc(&c->sweeps, 2 * sizeof(unsigned long long)) != cudaSuccess)
     return fail(c, TN_ENOMEM, "profiling counters");
-  if (c->profile) cudaMemsetAsync(c->sweeps, 0, 2 * sizeof(unsigned long long), s);
+  if (before[0] != c->arena || before[1] != c->inbuf || before[2] != c->expo) drop_graphs(c);
+  tnk::DevState ds{c->expo, c->status};
   unsigned long long* sw32 = c->profile ? c->sweeps : nullptr;
   unsigned long long* sw64 = c->profile ? c->sweeps + 1 : nullptr;
   auto ptr = [&](const tnp::PView& v) -> double* {
@@ -336,10 +391,30 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
 
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
   std::vector<int> ev_family;
+  // Every stream operation of one pass (gather, resets, steps), issued on s0.
+  // Under capture nothing runs; the side stream joins the capture through the
+  // fork event and is joined back before the pass ends.
+  auto enqueue = [&](cudaStream_t s0) -> int {
+  cudaStream_t s = s0;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < batch && e == cudaSuccess; ++b) {
+    const NetRec& nr = c->nets[c->insts[members[b]].net];
+    e = cudaMemcpyAsync(c->inbuf + (size_t)b * st.in_total, nr.d_data, sizeof(double) * st.in_total,
+                        cudaMemcpyDeviceToDevice, s);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->expo, 0, sizeof(long long) * batch, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int) * batch, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->tc_err, 0, sizeof(int), s);
+  if (e == cudaSuccess && c->profile) e = cudaMemsetAsync(c->sweeps, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gather inputs");
+  bool side_open = false;
   for (const tnp::Step& stp : plan.steps) {
     if (stop_op >= 0 && (stp.op_index > stop_op || stp.kind == tnp::ST_FINAL)) break;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (stp.join) cudaStreamWaitEvent(s, c->ev_join, 0);
+    if (stp.join && side_open) {
+      cudaStreamWaitEvent(s, c->ev_join, 0);
+      side_open = false;
+    }
     // a side-lane step forks from the main stream; profiling keeps everything on one stream
     const bool on_side = stp.lane == 1 && !c->profile;
     cudaStream_t ms = s;
@@ -421,7 +496,33 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
     if (on_side) {
       cudaEventRecord(c->ev_join, s);
       s = ms;
+      side_open = true;
     }
+  }
+  if (side_open) cudaStreamWaitEvent(s, c->ev_join, 0);
+  return TN_OK;
+  };
+
+  cudaStream_t s = c->stream;
+  const bool graphable = c->graph_mode && !c->profile && stop_op < 0;
+  GraphRec* gr = nullptr;
+  if (graphable) {
+    GraphKey key{plan.serial, c->buf_gen, members};
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+      c->graphs.emplace(key, GraphRec{});  // first call: eager; captured on the next
+    } else {
+      gr = &it->second;
+      if (!gr->exec && !gr->failed) capture_graph(c, gr, enqueue);
+    }
+  }
+  if (gr && gr->exec) {
+    e = cudaGraphLaunch(gr->exec, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    ++c->graph_replays;
+  } else {
+    rc = enqueue(s);
+    if (rc != TN_OK) return rc;
   }
   if (stop_op >= 0) {
     e = cudaStreamSynchronize(s);
@@ -504,10 +605,27 @@ void tn_destroy(tn_ctx* c) {
   cudaFree(c->out_sign);
   cudaFree(c->sweeps);
   cudaFree(c->tc_err);
+  for (auto& gx : c->graphs)
+    if (gx.second.exec) cudaGraphExecDestroy(gx.second.exec);
+  if (c->cap) cudaStreamDestroy(c->cap);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
+}
+
+int tn_set_graph_mode(tn_ctx* c, int mode) {
+  if (!c || mode < 0 || mode > 1) return fail(c, TN_EINVAL, "graph mode must be 0 or 1");
+  c->graph_mode = mode;
+  return TN_OK;
+}
+
+int tn_graph_info(const tn_ctx* c, int64_t* captured, int64_t* replays, int64_t* refused) {
+  if (!c) return TN_EINVAL;
+  if (captured) *captured = c->graph_captured;
+  if (replays) *replays = c->graph_replays;
+  if (refused) *refused = c->graph_refused;
+  return TN_OK;
 }
 
 int tn_set_stream(tn_ctx* c, void* stream) {

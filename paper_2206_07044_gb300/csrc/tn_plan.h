@@ -87,6 +87,7 @@ struct Plan {
   double gemm_flops = 0, qr_flops = 0, svd_flops = 0, permute_bytes = 0;
   int64_t max_jacobi_n = 0;
   PView final_scalar;
+  uint64_t serial = 0;       // set by the owner; distinct per plan built (keys captured graphs)
 };
 
 // Network structure (no data).

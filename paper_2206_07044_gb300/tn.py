@@ -52,6 +52,8 @@ SIGNATURES = {
     "tn_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
     "tn_destroy": (None, [C.c_void_p]),
     "tn_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tn_set_graph_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "tn_graph_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "tn_load_network": (C.c_int, [C.c_void_p, C.POINTER(NetworkDesc), C.POINTER(C.c_int)]),
     "tn_load_network_file": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int)]),
     "tn_set_network_data": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.c_int]),
@@ -223,6 +225,16 @@ class Context:
         p = PREC[prec] if isinstance(prec, str) else int(prec)
         self._check(self._L.tn_plan_stats_get(self._h, int(inst_id), int(chi), p, C.byref(st)))
         return {k: getattr(st, k) for k, _ in PlanStats._fields_}
+
+    def set_graph_mode(self, enable: bool) -> None:
+        """Replay whole schedules as CUDA graphs (default on) or launch every kernel eagerly."""
+        self._check(self._L.tn_set_graph_mode(self._h, 1 if enable else 0))
+
+    def graph_info(self) -> dict:
+        """Graphs captured, replays launched and captures refused since the context was made."""
+        v = [C.c_int64() for _ in range(3)]
+        self._check(self._L.tn_graph_info(self._h, *[C.byref(x) for x in v]))
+        return {"captured": v[0].value, "replays": v[1].value, "refused": v[2].value}
 
     def profile(self, enable: bool) -> None:
         self._check(self._L.tn_profile_enable(self._h, 1 if enable else 0))

@@ -322,3 +322,111 @@ def test_16x16_d4_chi64_batch_end_to_end(ctx):
         assert min(d[2] for d in want.diag) > 1e-8
         assert sg[s] == want.sign
         assert abs(lz[s] - want.logabs) <= TOL * abs(want.logabs), (s, lz[s], want.logabs)
+
+
+# ---------------------------------------------------------------------------
+# CUDA-graph replay of whole schedules
+
+
+def test_graph_replay_is_bitwise_eager(ctx):
+    """Eager launches, the capturing call and graph replays give identical bits."""
+    n, edges = nw.square_lattice(6, 7)
+    tree = tr.boundary_rows(6, 7)
+    nets = [nw.random_network(n, edges, 3, seed=40 + s) for s in range(3)]
+    ids = [ctx.load_tree(ctx.load_network(x), tree) for x in nets]
+    ctx.set_graph_mode(False)
+    ref = ctx.contract(ids, 9)
+    ctx.set_graph_mode(True)
+    before = ctx.graph_info()
+    runs = [ctx.contract(ids, 9) for _ in range(4)]   # eager, capture + launch, replay, replay
+    after = ctx.graph_info()
+    for lz, sg in runs:
+        assert np.array_equal(lz, ref[0]) and np.array_equal(sg, ref[1])
+    assert after["captured"] == before["captured"] + 1
+    assert after["replays"] == before["replays"] + 3
+    assert after["refused"] == before["refused"]
+    want = approx.contract(nets[1], tree, 9)
+    assert abs(ref[0][1] - want.logabs) <= TOL * abs(want.logabs)
+
+
+def test_graph_replay_sees_new_network_data(ctx):
+    """A replayed graph reads the instance's current entries (beta sweep through one graph)."""
+    n, edges = nw.square_lattice(6, 6)
+    tree = tr.boundary_rows(6, 6)
+    nid = ctx.load_network(nw.ising_network(n, edges, 0.2))
+    iid = ctx.load_tree(nid, tree)
+    before = ctx.graph_info()
+    for beta in (0.2, 0.3, 0.4, 0.5, 0.6):
+        net = nw.ising_network(n, edges, beta)
+        ctx.set_network_data(nid, net.data)
+        lz, _ = ctx.contract([iid], 4)
+        want = approx.contract(net, tree, 4)
+        assert abs(lz[0] - want.logabs) <= TOL * abs(want.logabs), beta
+    assert ctx.graph_info()["replays"] >= before["replays"] + 3
+
+
+def test_graph_dropped_when_buffers_grow():
+    """Growing the arena invalidates captured graphs; later replays stay correct."""
+    from paper_2206_07044_gb300 import Context, build
+    build.build()
+    ctx = Context(0)
+    n, edges = nw.square_lattice(5, 5)
+    tree = tr.boundary_rows(5, 5)
+    net = nw.random_network(n, edges, 3, seed=77)
+    small = [ctx.load_tree(ctx.load_network(net), tree)]
+    a = [ctx.contract(small, 5) for _ in range(3)]
+    n2, e2 = nw.square_lattice(12, 12)
+    big_tree = tr.boundary_rows(12, 12)
+    big = [ctx.load_tree(ctx.load_network(nw.random_network(n2, e2, 4, seed=s)), big_tree) for s in range(12)]
+    ctx.contract(big, 64)
+    b = [ctx.contract(small, 5) for _ in range(3)]
+    for lz, sg in a + b:
+        assert np.array_equal(lz, a[0][0]) and np.array_equal(sg, a[0][1])
+    info = ctx.graph_info()
+    ctx.close()
+    assert info["captured"] == 2 and info["refused"] == 0, info   # captured again after the drop
+    want = approx.contract(net, tree, 5)
+    assert abs(a[0][0][0] - want.logabs) <= TOL * abs(want.logabs)
+
+
+# ---------------------------------------------------------------------------
+# Reduced-precision GEMM forms (QR, SVD and absorbs stay FP64).  Tolerance of
+# each form: one unit roundoff of its GEMM input format on the relative log|Z|
+# (BF16 2^-8, TF32 2^-11), and the metric's 1e-6 gate for split TF32.
+
+FORM_TOL = {"bf16": 2.0 ** -8, "tf32": 2.0 ** -11, "tf32x3": 1e-6}
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16"])
+def test_mixed_forms_ising_8x8(ctx, prec):
+    n, edges = nw.square_lattice(8, 8)
+    net = nw.ising_network(n, edges, 0.44)
+    want = approx.contract(net, tr.boundary_rows(8, 8), 16)
+    got, sign = gpu_run(ctx, net, tr.boundary_rows(8, 8), 16, prec)
+    assert sign == want.sign
+    assert abs(got - want.logabs) <= FORM_TOL[prec] * abs(want.logabs), (prec, got, want.logabs)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16"])
+def test_mixed_forms_ising_16x16_batch(ctx, prec):
+    n, edges = nw.square_lattice(16, 16)
+    tree = tr.boundary_rows(16, 16)
+    betas = (0.3, 0.44)
+    nets = [nw.ising_network(n, edges, b) for b in betas]
+    ids = [ctx.load_tree(ctx.load_network(x), tree) for x in nets]
+    lz, sg = ctx.contract(ids, 32, prec)
+    for x, l, s in zip(nets, lz, sg):
+        want = approx.contract(x, tree, 32)
+        assert s == want.sign
+        assert abs(l - want.logabs) <= FORM_TOL[prec] * abs(want.logabs), (prec, l, want.logabs)
+
+
+def test_mixed_form_random_normal_within_format_roundoff(ctx):
+    """Sign-mixed entries: split TF32 stays within TF32-level error, TF32 within BF16-level."""
+    n, edges = nw.square_lattice(8, 8)
+    tree = tr.boundary_rows(8, 8)
+    net = nw.random_network(n, edges, 3, seed=5)
+    want = approx.contract(net, tree, 9)
+    for prec, tol in (("tf32x3", 2.0 ** -11), ("tf32", 2.0 ** -8)):
+        got, sign = gpu_run(ctx, net, tree, 9, prec)
+        assert abs(got - want.logabs) <= tol * abs(want.logabs), (prec, got, want.logabs)
