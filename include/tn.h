@@ -162,6 +162,35 @@ int tn_load_tree_file(tn_ctx* ctx, int net_id, const char* path, int* inst_id);
 int tn_contract_approx(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, int prec,
                        double* logabsz_out, int* sign_out);
 
+/* Gradient of the approximate log|Z| with respect to every input tensor
+ * (reverse-mode differentiation of Algorithm 1 as executed; the paper gives no
+ * adjoint).  Runs the same schedule as tn_contract_approx with every operand
+ * kept on the device, then its reverse pass on the GPU:
+ *   - a contraction C = A B returns A' = C' B^T and B' = A^T C';
+ *   - a rescale by 2^-e (exact, piecewise constant) returns 2^-e times;
+ *   - the root scalar x of ln|x| gets 1 / x;
+ *   - a compression returns the adjoint of the truncated SVD of X = A B
+ *     (A_bar = U_k s^1/2, B_bar = s^1/2 V_k^T up to a gauge the result does not
+ *     see), with F_ij = d / (d^2 + 1e-12 s_1^2), d = s_j^2 - s_i^2, and no
+ *     inverse for kept singular values at or below 1e-13 s_1; then A' = X' B^T,
+ *     B' = A^T X'.  All of it is evaluated in the bases of the forward QRs.
+ * The compressions' FP64 Jacobi keeps its rotations in this mode, so log|Z|
+ * may differ from tn_contract_approx's in the last bits.  In the mixed forms
+ * the contraction GEMMs of both passes run on the tensor cores; everything
+ * else stays FP64.
+ * grad_out[n] (n < n_inst) points to sum_t |T_t| doubles for instance n: the
+ * gradients of the input tensors packed in network order, each row-major over
+ * its listed bonds (the layout the network was loaded in); host pointers when
+ * on_device == 0, device pointers on the context's device otherwise.
+ * logabsz_out / sign_out as for tn_contract_approx.  Device memory: every
+ * intermediate of the forward pass stays allocated until the call returns.
+ * Errors: TN_EINVAL (bad ids, NULL pointers), TN_ENONFINITE when some Z == 0
+ * (log|Z| has no gradient there; the other instances' outputs are written),
+ * TN_ENOMEM, TN_ENOCONV, TN_ETIMEOUT, TN_ECUDA as for tn_contract_approx.
+ * Synchronises the context's stream before returning. */
+int tn_grad(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, int prec, double* logabsz_out,
+            int* sign_out, double* const* grad_out, int on_device);
+
 /* Schedule statistics of one instance at chi (no GPU work). */
 int tn_plan_stats_get(tn_ctx* ctx, int inst_id, int chi, int prec, tn_plan_stats* out);
 

@@ -40,16 +40,24 @@ __global__ void absmax_kernel(const double* __restrict__ X, int64_t n, int64_t b
 }
 
 __global__ void scale_kernel(double* __restrict__ X, int64_t n, int64_t bs,
-                             const unsigned long long* maxbits, long long* expo, int* status) {
+                             const unsigned long long* maxbits, long long* expo, int* status, int* e_out) {
   const int b = blockIdx.y;
   const double m = __longlong_as_double((long long)maxbits[b]);
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   if (!isfinite(m)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(status + b, -7);
+    if (lead) {
+      atomicExch(status + b, -7);
+      if (e_out) e_out[b] = 0;
+    }
     return;
   }
-  if (m == 0.0) return;
+  if (m == 0.0) {
+    if (lead && e_out) e_out[b] = 0;
+    return;
+  }
   int e;
   frexp(m, &e);
+  if (lead && e_out) e_out[b] = e;
   const double sc = ldexp(1.0, -e);
   double* x = X + (int64_t)b * bs;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -92,13 +100,13 @@ int grid_for(int64_t n) {
 }  // namespace
 
 cudaError_t rescale_f64(double* X, int64_t n, int64_t bs, unsigned long long* maxbits, DevState st,
-                        int batch, cudaStream_t s) {
+                        int batch, cudaStream_t s, int* e_out) {
   if (n <= 0 || batch <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long) * batch, s);
   if (e != cudaSuccess) return e;
   dim3 grid(grid_for(n), batch);
   absmax_kernel<<<grid, 256, 0, s>>>(X, n, bs, maxbits);
-  scale_kernel<<<grid, 256, 0, s>>>(X, n, bs, maxbits, st.expo, st.status);
+  scale_kernel<<<grid, 256, 0, s>>>(X, n, bs, maxbits, st.expo, st.status, e_out);
   return cudaGetLastError();
 }
 

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kThreads) qr_cluster_kernel(int m, int n, View
 // memory.
 __global__ void __launch_bounds__(kThreads) apply_q_kernel(int m, int n, const double* Wall,
                                                            int64_t w_bs, const double* taus,
-                                                           double* Xall, int64_t x_bs, int k) {
+                                                           double* Xall, int64_t x_bs, int k, int trans) {
   const int b = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const double* W = Wall + (int64_t)b * w_bs;
@@ -167,7 +167,9 @@ __global__ void __launch_bounds__(kThreads) apply_q_kernel(int m, int n, const d
   extern __shared__ double vs[];
   const bool stage_v = (m <= kVSmem);
   const int rmin = m < n ? m : n;
-  for (int j = rmin - 1; j >= 0; --j) {
+  // Q = H_0 H_1 ... H_{r-1}: Q X applies H_{r-1} first, Q^T X applies H_0 first
+  for (int it = 0; it < rmin; ++it) {
+    const int j = trans ? it : rmin - 1 - it;
     const double t = tau[j];
     if (t == 0.0) continue;
     const double* v = W + (int64_t)j * m;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) apply_q_kernel(int m, int n, const d
 }  // namespace
 
 cudaError_t apply_q_f64(int m, int n, const double* work, int64_t work_bs, double* X, int64_t x_bs, int k,
-                        int batch, cudaStream_t s) {
+                        int batch, cudaStream_t s, int trans) {
   if (m <= 0 || n <= 0 || k <= 0 || batch <= 0) return cudaSuccess;
   if (batch > 65535) return cudaErrorInvalidValue;
   const double* taus = work + (int64_t)batch * work_bs;
@@ -201,7 +203,7 @@ cudaError_t apply_q_f64(int m, int n, const double* work, int64_t work_bs, doubl
   }
   const int per_cta = kThreads / 32;
   dim3 grid((k + per_cta - 1) / per_cta, batch);
-  apply_q_kernel<<<grid, kThreads, smem, s>>>(m, n, work, work_bs, taus, X, x_bs, k);
+  apply_q_kernel<<<grid, kThreads, smem, s>>>(m, n, work, work_bs, taus, X, x_bs, k, trans);
   return cudaGetLastError();
 }
 

@@ -45,8 +45,9 @@ struct InstRec {
 struct PlanKey {
   uint64_t hash;
   int chi, prec;
+  int grad;  // 1: the plan also runs the reverse pass
   bool operator<(const PlanKey& o) const {
-    return std::tie(hash, chi, prec) < std::tie(o.hash, o.chi, o.prec);
+    return std::tie(hash, chi, prec, grad) < std::tie(o.hash, o.chi, o.prec, o.grad);
   }
 };
 
@@ -68,8 +69,10 @@ struct GraphRec {
   bool failed = false;  // capture was refused: this key always runs eagerly
 };
 
-const char* kFamily[] = {"permute", "gemm_f64", "qr_f64", "jacobi_f64", "select_scale", "rescale",
-                         "finalize", "to_f32", "jacobi_f32", "to_f64", "copy", "apply_q_f64", "gemm_tc"};
+const char* kFamily[] = {"permute", "gemm_f64",   "qr_f64",     "jacobi_f64",  "select_scale", "rescale",
+                         "finalize", "to_f32",     "jacobi_f32", "to_f64",      "copy",         "apply_q_f64",
+                         "gemm_tc",  "scale_pow2", "final_grad", "svd_factors", "svd_adj_core", "copy2d"};
+static_assert(sizeof(kFamily) / sizeof(kFamily[0]) == tnp::kNumStepKinds, "one family name per step kind");
 constexpr int kNumFamily = tnp::kNumStepKinds;
 
 }  // namespace
@@ -85,6 +88,11 @@ struct tn_ctx {
   size_t arena_bytes = 0;
   double* inbuf = nullptr;
   size_t inbuf_bytes = 0;
+  // reverse pass: adjoints of the inputs (input-block layout) and the rescale exponent tape
+  double* ginbuf = nullptr;
+  size_t ginbuf_bytes = 0;
+  int* etape = nullptr;
+  size_t etape_bytes = 0;
   // per-instance scratch
   int scratch_batch = 0;
   long long* expo = nullptr;
@@ -293,14 +301,14 @@ int ensure_scratch(tn_ctx* c, int batch) {
   return TN_OK;
 }
 
-const tnp::Plan* get_plan(tn_ctx* c, int inst, int chi, int prec, int* rc) {
-  PlanKey key{c->insts[inst].hash, chi, prec};
+const tnp::Plan* get_plan(tn_ctx* c, int inst, int chi, int prec, int* rc, bool grad = false) {
+  PlanKey key{c->insts[inst].hash, chi, prec, grad ? 1 : 0};
   auto it = c->plans.find(key);
   if (it != c->plans.end() && same_group(c, it->second.inst_proto, inst)) return &it->second.plan;
   CachedPlan cp;
   cp.inst_proto = inst;
   const InstRec& r = c->insts[inst];
-  std::string err = tnp::build_plan(c->nets[r.net].st, r.ops, r.n_inputs, chi, prec, &cp.plan);
+  std::string err = tnp::build_plan(c->nets[r.net].st, r.ops, r.n_inputs, chi, prec, &cp.plan, grad);
   if (!err.empty()) {
     *rc = fail(c, TN_EFORMAT, "plan: " + err);
     return nullptr;
@@ -361,13 +369,21 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   if (batch > 65535) return fail(c, TN_EINVAL, "more than 65535 instances in one batch");
   const tnp::Structure& st = c->nets[c->insts[members[0]].net].st;
   cudaError_t e;
-  const void* before[3] = {c->arena, c->inbuf, c->expo};
+  const void* before[5] = {c->arena, c->inbuf, c->expo, c->ginbuf, c->etape};
   const size_t arena_need = sizeof(double) * (size_t)std::max<int64_t>(plan.arena_units, 1) * batch;
   if ((e = ensure(&c->arena, &c->arena_bytes, arena_need)) != cudaSuccess)
     return fail(c, TN_ENOMEM, "arena allocation of " + std::to_string(arena_need) + " bytes failed");
   const size_t in_need = sizeof(double) * (size_t)std::max<int64_t>(st.in_total, 1) * batch;
   if ((e = ensure(&c->inbuf, &c->inbuf_bytes, in_need)) != cudaSuccess)
     return fail(c, TN_ENOMEM, "input buffer allocation failed");
+  if (plan.grad) {
+    const size_t g_need = sizeof(double) * (size_t)std::max<int64_t>(plan.in_total, 1) * batch;
+    if ((e = ensure(&c->ginbuf, &c->ginbuf_bytes, g_need)) != cudaSuccess)
+      return fail(c, TN_ENOMEM, "input-adjoint buffer allocation failed");
+    const size_t t_need = sizeof(int) * (size_t)std::max(plan.n_slots, 1) * batch;
+    if ((e = ensure(&c->etape, &c->etape_bytes, t_need)) != cudaSuccess)
+      return fail(c, TN_ENOMEM, "exponent tape allocation failed");
+  }
   int rc = ensure_scratch(c, batch);
   if (rc != TN_OK) return rc;
   if (!c->side) {
@@ -379,12 +395,17 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   if (!c->tc_err && cudaMalloc(&c->tc_err, sizeof(int)) != cudaSuccess) return fail(c, TN_ENOMEM, "error word");
   if (c->profile && !c->sweeps && cudaMalloc(&c->sweeps, 2 * sizeof(unsigned long long)) != cudaSuccess)
     return fail(c, TN_ENOMEM, "profiling counters");
-  if (before[0] != c->arena || before[1] != c->inbuf || before[2] != c->expo) drop_graphs(c);
+  if (before[0] != c->arena || before[1] != c->inbuf || before[2] != c->expo || before[3] != c->ginbuf ||
+      before[4] != c->etape)
+    drop_graphs(c);
   tnk::DevState ds{c->expo, c->status};
   unsigned long long* sw32 = c->profile ? c->sweeps : nullptr;
   unsigned long long* sw64 = c->profile ? c->sweeps + 1 : nullptr;
   auto ptr = [&](const tnp::PView& v) -> double* {
-    return v.buf == tnp::BUF_INPUT ? c->inbuf + v.off : c->arena + v.off * batch;
+    double* base = v.buf == tnp::BUF_INPUT ? c->inbuf + v.off
+                   : v.buf == tnp::BUF_GIN ? c->ginbuf + v.off
+                                           : c->arena + v.off * batch;
+    return base + v.eo;
   };
   auto cview = [&](const tnp::PView& v) { return tnk::View{ptr(v), v.rs, v.cs, v.bs}; };
   auto wview = [&](const tnp::PView& v) { return tnk::ViewW{ptr(v), v.rs, v.cs, v.bs}; };
@@ -469,17 +490,37 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
                                   stp.no_v ? ptr(stp.work) : nullptr, stp.work.bs);
         break;
       case tnp::ST_APPLYQ:
-        e = tnk::apply_q_f64(stp.m, stp.n, ptr(stp.work), stp.work.bs, ptr(stp.C), stp.C.bs, stp.k, batch, s);
+        e = tnk::apply_q_f64(stp.m, stp.n, ptr(stp.work), stp.work.bs, ptr(stp.C), stp.C.bs, stp.k, batch, s,
+                             stp.flag);
         break;
       case tnp::ST_GEMM_TC:
         e = tnk::gemm_tc(stp.m, stp.n, stp.k, 1.0, cview(stp.A), cview(stp.B), wview(stp.C), batch, stp.tc_mode,
                          ptr(stp.work), sizeof(double) * (size_t)stp.work.bs * batch, c->tc_err, s);
         break;
       case tnp::ST_RESCALE:
-        e = tnk::rescale_f64(ptr(stp.C), stp.count, stp.C.bs, c->maxbits, ds, batch, s);
+        e = tnk::rescale_f64(ptr(stp.C), stp.count, stp.C.bs, c->maxbits, ds, batch, s,
+                             stp.slot >= 0 ? c->etape + (size_t)stp.slot * batch : nullptr);
         break;
       case tnp::ST_FINAL:
         e = tnk::finalize_f64(ptr(stp.C), stp.C.bs, ds, c->out_log, c->out_sign, batch, s);
+        break;
+      case tnp::ST_SCALE_POW2:
+        e = tnk::scale_pow2_f64(ptr(stp.C), stp.count, stp.C.bs, c->etape + (size_t)stp.slot * batch, batch, s);
+        break;
+      case tnp::ST_FINAL_GRAD:
+        e = tnk::final_grad_f64(ptr(stp.C), stp.C.bs, ptr(stp.out1), stp.out1.bs, batch, s);
+        break;
+      case tnp::ST_SVD_FACTORS:
+        e = tnk::svd_factors_f64(stp.m, stp.n, stp.k, stp.flag, ptr(stp.C), stp.C.bs, ptr(stp.aux1), stp.aux1.bs,
+                                 ptr(stp.aux2), stp.aux2.bs, ptr(stp.out1), stp.out1.bs, ptr(stp.out2), stp.out2.bs,
+                                 ptr(stp.work), stp.work.bs, ptr(stp.A), stp.A.bs, ptr(stp.B), stp.B.bs, batch, s);
+        break;
+      case tnp::ST_SVD_ADJ_CORE:
+        e = tnk::svd_adjoint_core_f64(stp.n, stp.k, ptr(stp.A), stp.A.bs, ptr(stp.B), stp.B.bs, ptr(stp.work),
+                                      stp.work.bs, ptr(stp.C), stp.C.bs, batch, s);
+        break;
+      case tnp::ST_COPY2D:
+        e = tnk::copy2d_f64(stp.m, stp.n, cview(stp.A), wview(stp.C), batch, s);
         break;
       default:
         e = cudaErrorInvalidValue;
@@ -597,6 +638,8 @@ void tn_destroy(tn_ctx* c) {
   for (auto& n : c->nets) cudaFree(n.d_data);
   cudaFree(c->arena);
   cudaFree(c->inbuf);
+  cudaFree(c->ginbuf);
+  cudaFree(c->etape);
   cudaFree(c->expo);
   cudaFree(c->status);
   cudaFree(c->jac_ws);
@@ -777,6 +820,61 @@ int tn_contract_approx(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int 
       sign_out[pos[m]] = sg[m];
     }
   }
+  return TN_OK;
+}
+
+int tn_grad(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, double* logabsz_out, int* sign_out,
+            double* const* grad_out, int on_device) {
+  if (!c || !inst_ids || !logabsz_out || !sign_out || !grad_out || n_inst < 1)
+    return fail(c, TN_EINVAL, "bad arguments");
+  if (chi < 1) return fail(c, TN_EINVAL, "chi must be >= 1");
+  if (prec < TN_F64 || prec > TN_TF32X3) return fail(c, TN_EINVAL, "unknown precision form");
+  for (int q = 0; q < n_inst; ++q) {
+    if (inst_ids[q] < 0 || inst_ids[q] >= (int)c->insts.size()) return fail(c, TN_EINVAL, "unknown instance id");
+    if (!grad_out[q]) return fail(c, TN_EINVAL, "grad_out has a NULL entry");
+  }
+  DeviceGuard g(c->device);
+  std::vector<bool> done(n_inst, false);
+  int zero_at = -1;
+  for (int q = 0; q < n_inst; ++q) {
+    if (done[q]) continue;
+    std::vector<int> members, pos;
+    for (int r = q; r < n_inst; ++r)
+      if (!done[r] && same_group(c, inst_ids[q], inst_ids[r])) {
+        members.push_back(inst_ids[r]);
+        pos.push_back(r);
+        done[r] = true;
+      }
+    int rc = TN_OK;
+    const tnp::Plan* plan = get_plan(c, inst_ids[q], chi, prec, &rc, true);
+    if (!plan) return rc;
+    std::vector<double> lg(members.size());
+    std::vector<int> sg(members.size());
+    rc = run_group(c, *plan, members, lg.data(), sg.data());
+    if (rc != TN_OK) return rc;
+    // the adjoint block is padded like the input block; hand it out packed
+    const tnp::Structure& st = c->nets[c->insts[members[0]].net].st;
+    const int64_t nt = plan->in_total;
+    for (size_t m = 0; m < members.size(); ++m) {
+      logabsz_out[pos[m]] = lg[m];
+      sign_out[pos[m]] = sg[m];
+      if (sg[m] == 0 && zero_at < 0) zero_at = pos[m];
+      int64_t packed = 0;
+      for (size_t t = 0; t < st.bonds.size(); ++t) {
+        int64_t sz = 1;
+        for (int b : st.bonds[t]) sz *= st.bond_dims[b];
+        cudaError_t e = cudaMemcpyAsync(grad_out[pos[m]] + packed, c->ginbuf + (size_t)m * nt + st.in_off[t],
+                                        sizeof(double) * sz,
+                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "gradient copy-out");
+        packed += sz;
+      }
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "gradient copy-out");
+  }
+  if (zero_at >= 0)
+    return fail(c, TN_ENONFINITE, "Z = 0 for instance " + std::to_string(zero_at) + ": log|Z| has no gradient");
   return TN_OK;
 }
 

@@ -73,13 +73,14 @@ cudaError_t select_scale_f64(int m, int n, int k, const double* G, int64_t g_bs,
 
 // X[b] <- Q[b] X[b], Q the Householder product a qr_r_f64 call left in `work`
 // (same m, n, work, work_bs and batch).  X: m x k column-major (ld m).
+// trans = 1: X[b] <- Q[b]^T X[b] instead.
 cudaError_t apply_q_f64(int m, int n, const double* work, int64_t work_bs, double* X, int64_t x_bs, int k,
-                        int batch, cudaStream_t s);
+                        int batch, cudaStream_t s, int trans = 0);
 
 // X[b] *= 2^-e_b with e_b the binary exponent of max|X[b]|; st.expo[b] += e_b.
-// maxbits: [batch] device scratch.
+// maxbits: [batch] device scratch; e_out (optional, [batch]) receives e_b.
 cudaError_t rescale_f64(double* X, int64_t n, int64_t bs, unsigned long long* maxbits, DevState st,
-                        int batch, cudaStream_t s);
+                        int batch, cudaStream_t s, int* e_out = nullptr);
 
 // Final: out_log[b] = ln|x[b]| + expo[b] ln 2 (device arrays), out_sign[b].
 cudaError_t finalize_f64(const double* x, int64_t bs, DevState st, double* out_log, int* out_sign,
@@ -97,5 +98,36 @@ cudaError_t set_identity_f64(double* V, int n, int64_t bs, int batch, cudaStream
 size_t gemm_tc_workspace_bytes(int m, int n, int k, int mode, int batch);
 cudaError_t gemm_tc(int m, int n, int k, double alpha, View A, View B, ViewW C, int batch, int mode,
                     void* workspace, size_t ws_bytes, int* err, cudaStream_t s);
+
+// ---- reverse pass (d log|Z| / d inputs)
+
+// X[b] *= 2^-e[b] (the adjoint of a rescale that divided by 2^e[b]).
+cudaError_t scale_pow2_f64(double* X, int64_t n, int64_t bs, const int* e, int batch, cudaStream_t s);
+
+// g[b] = 1 / x[b]: the adjoint of ln|x| for the final scalar.
+cudaError_t final_grad_f64(const double* x, int64_t xbs, double* g, int64_t gbs, int batch, cudaStream_t s);
+
+// From a Jacobi SVD of J (m x n column-major, m >= n: G = J V holds sigma_i u_i,
+// V the right vectors, sig unsorted) build, in descending order of sigma
+// (ties by index, as select_scale_f64 ranks them), the factors of M = J when
+// tall, else M = J^T:  U (rows_u x n, ld rows_u), W (rows_w x n, ld rows_w)
+// with M = U diag(s) W^T, s (n), and the first k columns scaled by s^-1/2:
+// Us (rows_u x k), Ws (rows_w x k).  Columns with sigma <= 1e-13 sigma_max get
+// u_i = 0 (when u comes from G) and s^-1/2 = 0.
+cudaError_t svd_factors_f64(int m, int n, int k, int tall, const double* G, int64_t g_bs, const double* V,
+                            int64_t v_bs, const double* sig, int64_t sig_bs, double* U, int64_t u_bs, double* W,
+                            int64_t w_bs, double* s_out, int64_t s_bs, double* Us, int64_t us_bs, double* Ws,
+                            int64_t ws_bs, int batch, cudaStream_t s);
+
+// Core matrix of the truncated-SVD adjoint (q x q column-major):
+//   C_ij = F_ij (a_ij - a_ji) s_j + s_i F_ij (b_ij - b_ji) + [i == j < k] (P_ii + Q_ii) / (2 s_i^1/2)
+// with a_ij = P_ij s_j^1/2, b_ij = Q_ij s_j^1/2 for j < k (0 otherwise),
+// F_ij = d / (d^2 + 1e-12 s_0^2), d = s_j^2 - s_i^2 (F_ii = 0), s descending;
+// P, Q: q x k column-major.
+cudaError_t svd_adjoint_core_f64(int q, int k, const double* P, int64_t p_bs, const double* Q, int64_t q_bs,
+                                 const double* s, int64_t s_bs, double* C, int64_t c_bs, int batch, cudaStream_t st);
+
+// Y[b] (m x n) <- X[b] (m x n), both strided views.
+cudaError_t copy2d_f64(int m, int n, View X, ViewW Y, int batch, cudaStream_t s);
 
 }  // namespace tnk

@@ -147,7 +147,9 @@ extern "C" int tn_contract_approx_noalloc(const tn_network_desc* net, const tn_t
   if (ce == cudaSuccess) ce = cudaMemsetAsync(status, 0, sizeof(int), s);
   if (ce != cudaSuccess) return set_err(err_msg, err_cap, TN_ECUDA, std::string("upload: ") + cudaGetErrorString(ce));
   tnk::DevState ds{expo, status};
-  auto ptr = [&](const tnp::PView& v) -> double* { return v.buf == tnp::BUF_INPUT ? inbuf + v.off : arena + v.off; };
+  auto ptr = [&](const tnp::PView& v) -> double* {
+    return (v.buf == tnp::BUF_INPUT ? inbuf + v.off : arena + v.off) + v.eo;
+  };
   auto cview = [&](const tnp::PView& v) { return tnk::View{ptr(v), v.rs, v.cs, v.bs}; };
   auto wview = [&](const tnp::PView& v) { return tnk::ViewW{ptr(v), v.rs, v.cs, v.bs}; };
   const int batch = 1;

@@ -23,6 +23,7 @@
 #include "tn_kernels.h"
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <unordered_map>
 #include <unordered_set>
@@ -122,6 +123,17 @@ struct Builder {
   std::unordered_map<int, int> cur;  // tensor id -> value index
   std::vector<int64_t> dim;          // bond sizes (grows with new bonds)
   int op_index = -1;
+  // reverse pass: the forward keeps every value (keep), each forward op pushes
+  // a closure that emits its reverse steps, run in reverse order at the end
+  bool grad = false;
+  bool keep = false;
+  bool in_bwd = false;
+  std::vector<std::function<void()>> bwd;
+  std::unordered_map<int, PView> gv;  // value index -> buffer of its adjoint
+
+  void rel(int64_t off, int64_t size) {
+    if (!keep) arena.release(off, size);
+  }
 
   PView base_view(const Value& v) const {
     PView p;
@@ -159,7 +171,7 @@ struct Builder {
   }
   void release_value(int vi) {
     Value& v = vals[vi];
-    if (v.buf == BUF_ARENA) arena.release(v.off, v.size);
+    if (v.buf == BUF_ARENA) rel(v.off, v.size);
   }
   void add(Step st) {
     st.op_index = op_index;
@@ -197,6 +209,10 @@ struct Builder {
     st.beta = beta;
     st.flops = overhead ? 0.0 : 2.0 * m * n * (double)k;
     st.bytes = 8.0 * ((double)m * k + (double)k * n + (double)m * n);
+    if (in_bwd) {
+      plan->bwd_flops += 2.0 * m * n * (double)k;
+      st.flops = 0.0;
+    }
     plan->gemm_flops += st.flops;
     add(st);
   }
@@ -219,17 +235,78 @@ struct Builder {
     st.work = temp((per + 7) / 8, &off);
     st.flops = count_flops ? 2.0 * m * n * (double)k : 0.0;
     st.bytes = 8.0 * ((double)m * k + (double)k * n + (double)m * n);
+    if (in_bwd) {
+      plan->bwd_flops += 2.0 * m * n * (double)k;
+      st.flops = 0.0;
+    }
     plan->gemm_flops += st.flops;
     add(st);
-    arena.release(off, (per + 7) / 8);
+    rel(off, (per + 7) / 8);
   }
-  void rescale(int vi) {
+  // returns the exponent-tape slot (reverse-pass plans) or -1
+  int rescale(int vi) {
     Step st;
     st.kind = ST_RESCALE;
     st.C = base_view(vals[vi]);
     st.count = vals[vi].size;
     st.bytes = 24.0 * (double)vals[vi].size;
+    if (grad) st.slot = plan->n_slots++;
     add(st);
+    return st.slot;
+  }
+
+  // ---- reverse-pass helpers
+  // Adjoint buffer of value vi (same layout as the value); inputs map to BUF_GIN.
+  PView gview(int vi) {
+    auto it = gv.find(vi);
+    if (it != gv.end()) return it->second;
+    const Value& v = vals[vi];
+    PView p;
+    if (v.buf == BUF_INPUT) {
+      p.buf = BUF_GIN;
+      p.off = v.off;
+      p.bs = v.bs;
+    } else {
+      int64_t off;
+      p = temp(v.size, &off);
+    }
+    gv[vi] = p;
+    return p;
+  }
+  void gfree(int vi) {
+    auto it = gv.find(vi);
+    if (it == gv.end()) return;
+    if (it->second.buf == BUF_ARENA) arena.release(it->second.off, vals[vi].size);
+    gv.erase(it);
+  }
+  void scale_pow2(const PView& g, int64_t count, int slot) {
+    Step st;
+    st.kind = ST_SCALE_POW2;
+    st.C = g;
+    st.count = count;
+    st.slot = slot;
+    st.bytes = 16.0 * (double)count;
+    add(st);
+  }
+  // adjoint of `tmp = permute(orig)`: orig' = inverse permutation of tmp'
+  void permute_back(int tmp, int orig) {
+    Step st;
+    st.kind = ST_PERMUTE;
+    st.src = gview(tmp);
+    st.dst = gview(orig);
+    const std::vector<int>& tb = vals[tmp].bonds;
+    for (int b : tb) st.in_dims.push_back(dim[b]);
+    for (int b : vals[orig].bonds) st.perm.push_back((int)(std::find(tb.begin(), tb.end(), b) - tb.begin()));
+    st.count = vals[tmp].size;
+    st.bytes = 16.0 * (double)st.count;
+    add(st);
+  }
+  // C = A B in the plan's form (tensor cores in the mixed forms)
+  void gemm_form(int m, int n, int k, PView A, PView B, PView C) {
+    if (mixed())
+      gemm_tc_step(m, n, k, A, B, C, false);
+    else
+      gemm(m, n, k, A, B, C);
   }
 
   // Shared bonds in the order of `order_src`, plus the remaining bonds of each side.
@@ -303,7 +380,37 @@ struct Builder {
       gemm_tc_step((int)m, (int)n, (int)kk, A, B, C, true);
     else
       gemm((int)m, (int)n, (int)kk, A, B, C);
-    rescale(ic);
+    const int slot = rescale(ic);
+    if (grad) {
+      const int my_op = op_index;
+      bwd.push_back([=, this]() {
+        // C = A B: A' = C' B^T, B' = A^T C' (C' unscaled first)
+        op_index = my_op;
+        PView gC = gview(ic);
+        scale_pow2(gC, m * n, slot);
+        gC.rs = n;
+        gC.cs = 1;
+        PView gA = gview(ia), Bt = B;
+        gA.rs = A.rs;
+        gA.cs = A.cs;
+        std::swap(Bt.rs, Bt.cs);
+        gemm_form((int)m, (int)kk, (int)n, gC, Bt, gA);
+        PView gB = gview(ib), At = A;
+        gB.rs = B.rs;
+        gB.cs = B.cs;
+        std::swap(At.rs, At.cs);
+        gemm_form((int)kk, (int)n, (int)m, At, gC, gB);
+        gfree(ic);
+        if (ia != ia0) {
+          permute_back(ia, ia0);
+          gfree(ia);
+        }
+        if (ib != ib0) {
+          permute_back(ib, ib0);
+          gfree(ib);
+        }
+      });
+    }
     for (int t : tmps) release_value(t);
     release_value(ia0);
     release_value(ib0);
@@ -315,6 +422,162 @@ struct Builder {
     plan->consumed.push_back({op_index, j});
     plan->n_contractions++;
     return "";
+  }
+
+  // Reverse steps of one compression (see k_adjoint.cu for the algebra).
+  // A (DA x dab) and B (dab x DB) are the forward operand views, RA (rA x dab)
+  // and LB (dab x rB) the triangular factors (A / B themselves when no QR ran),
+  // G, V, sig the Jacobi outputs of the core (Jm x Jn, tall: core = M, else M^T).
+  void compress_adjoint(int ia, int ib, int ia0, int ib0, PView A, PView B, int64_t DA, int64_t DB, int64_t dab,
+                        int64_t rA, int64_t rB, int64_t kk, bool tall, int64_t Jm, int64_t Jn, PView workA,
+                        PView workB, PView RA, PView LB, PView G, PView V, PView sig, int na, int nbv, int slot_a,
+                        int slot_b) {
+    const int64_t q = Jn;
+    std::vector<std::pair<int64_t, int64_t>> tr;
+    auto tmp = [&](int64_t size) {
+      int64_t off;
+      PView p = temp(size, &off);
+      tr.push_back({off, size});
+      return p;
+    };
+    auto cm = [](PView p, int64_t ld) {  // column-major with leading dimension ld
+      p.rs = 1;
+      p.cs = ld;
+      return p;
+    };
+    auto tp = [](PView p) {
+      std::swap(p.rs, p.cs);
+      return p;
+    };
+    // incoming adjoints of A_bar (DA x kk) and B_bar^T (DB x kk), unscaled, then in the QR bases
+    PView gAb = gview(na), gBb = gview(nbv);
+    scale_pow2(gAb, DA * kk, slot_a);
+    scale_pow2(gBb, DB * kk, slot_b);
+    auto applyq = [&](int64_t mm, const PView& work, const PView& X, int64_t ncols, int trans) {
+      Step st;
+      st.kind = ST_APPLYQ;
+      st.m = (int)mm;
+      st.n = (int)dab;
+      st.k = (int)ncols;
+      st.work = work;
+      st.C = X;
+      st.flag = trans;
+      st.bytes = 8.0 * (mm * dab + 2.0 * mm * ncols);
+      add(st);
+    };
+    if (DA > dab) applyq(DA, workA, gAb, kk, 1);
+    if (DB > dab) applyq(DB, workB, gBb, kk, 1);
+    // sorted singular factors of the core M = U diag(s) W^T (rA x rB)
+    PView U = cm(tmp(rA * q), rA), W = cm(tmp(rB * q), rB), sv = tmp(q);
+    PView Us = cm(tmp(rA * kk), rA), Ws = cm(tmp(rB * kk), rB);
+    {
+      Step st;
+      st.kind = ST_SVD_FACTORS;
+      st.m = (int)Jm;
+      st.n = (int)Jn;
+      st.k = (int)kk;
+      st.flag = tall ? 1 : 0;
+      st.C = G;
+      st.aux1 = V;
+      st.aux2 = sig;
+      st.out1 = U;
+      st.out2 = W;
+      st.work = sv;
+      st.A = Us;
+      st.B = Ws;
+      add(st);
+    }
+    PView dU = cm(gAb, DA), dV = cm(gBb, DB);   // top rA / rB rows
+    PView P = cm(tmp(q * kk), q), Qm = cm(tmp(q * kk), q);
+    gemm((int)q, (int)kk, (int)rA, tp(U), dU, P);
+    gemm((int)q, (int)kk, (int)rB, tp(W), dV, Qm);
+    PView Cc = cm(tmp(q * q), q);
+    {
+      Step st;
+      st.kind = ST_SVD_ADJ_CORE;
+      st.n = (int)q;
+      st.k = (int)kk;
+      st.A = P;
+      st.B = Qm;
+      st.work = sv;
+      st.C = Cc;
+      add(st);
+    }
+    // dU <- dU - U P, dV <- dV - W Q (in place: the complements inside the core)
+    gemm((int)rA, (int)kk, (int)q, U, P, dU, -1.0, 1.0);
+    gemm((int)rB, (int)kk, (int)q, W, Qm, dV, -1.0, 1.0);
+    // D11 = U (C W^T) + dU Ws^T + Us dV^T
+    PView T1 = cm(tmp(q * rB), q), D11 = cm(tmp(rA * rB), rA);
+    gemm((int)q, (int)rB, (int)q, Cc, tp(W), T1);
+    gemm((int)rA, (int)rB, (int)q, U, T1, D11);
+    gemm((int)rA, (int)rB, (int)kk, dU, tp(Ws), D11, 1.0, 1.0);
+    gemm((int)rA, (int)rB, (int)kk, Us, tp(dV), D11, 1.0, 1.0);
+    // A' (DA x dab) into the adjoint of A's value, with A's strides
+    const PView RBp = tp(LB);   // R_B' = L_B^T (rB x dab)
+    PView gA = gview(ia);
+    gA.rs = A.rs;
+    gA.cs = A.cs;
+    if (DA > dab) {
+      PView ZA = cm(tmp(DA * dab), DA);
+      gemm((int)rA, (int)dab, (int)rB, D11, RBp, ZA);
+      if (DA > rA) {
+        PView HB = cm(tmp(kk * dab), kk);
+        gemm((int)kk, (int)dab, (int)rB, tp(Ws), RBp, HB);
+        PView WA = dU, ZAb = ZA;
+        WA.eo = rA;
+        ZAb.eo = rA;
+        gemm((int)(DA - rA), (int)dab, (int)kk, WA, HB, ZAb);
+      }
+      applyq(DA, workA, ZA, dab, 0);
+      Step cp;
+      cp.kind = ST_COPY2D;
+      cp.m = (int)DA;
+      cp.n = (int)dab;
+      cp.A = ZA;
+      cp.C = gA;
+      cp.bytes = 16.0 * DA * dab;
+      add(cp);
+    } else {
+      gemm((int)DA, (int)dab, (int)rB, D11, RBp, gA);
+    }
+    // B'^T (DB x dab) into the adjoint of B's value, through B's transposed strides
+    PView gBt = gview(ib);
+    gBt.rs = B.cs;
+    gBt.cs = B.rs;
+    if (DB > dab) {
+      PView ZB = cm(tmp(DB * dab), DB);
+      gemm((int)rB, (int)dab, (int)rA, tp(D11), RA, ZB);
+      if (DB > rB) {
+        PView HA = cm(tmp(kk * dab), kk);
+        gemm((int)kk, (int)dab, (int)rA, tp(Us), RA, HA);
+        PView WB = dV, ZBb = ZB;
+        WB.eo = rB;
+        ZBb.eo = rB;
+        gemm((int)(DB - rB), (int)dab, (int)kk, WB, HA, ZBb);
+      }
+      applyq(DB, workB, ZB, dab, 0);
+      Step cp;
+      cp.kind = ST_COPY2D;
+      cp.m = (int)DB;
+      cp.n = (int)dab;
+      cp.A = ZB;
+      cp.C = gBt;
+      cp.bytes = 16.0 * DB * dab;
+      add(cp);
+    } else {
+      gemm((int)DB, (int)dab, (int)rA, tp(D11), RA, gBt);
+    }
+    for (auto& t : tr) arena.release(t.first, t.second);
+    gfree(na);
+    gfree(nbv);
+    if (ia != ia0) {
+      permute_back(ia, ia0);
+      gfree(ia);
+    }
+    if (ib != ib0) {
+      permute_back(ib, ib0);
+      gfree(ib);
+    }
   }
 
   std::string compress(int i, int j) {
@@ -477,7 +740,9 @@ struct Builder {
       st.aux1 = V;
       st.aux2 = sig;
       st.init_v = 0;
-      st.no_v = 1;   // V_k is recovered after the sweeps from M^T U_k (a GEMM), see below
+      // V_k is recovered after the sweeps from M^T U_k (a GEMM), see below; the
+      // reverse pass needs every right vector accurately, so it keeps V
+      st.no_v = grad ? 0 : 1;
       st.jac_tol = 1e-8;
       st.flops = svd_flops((double)rA, (double)rB);
       st.bytes = 8.0 * (2.0 * Jm * Jn + 2.0 * Jn * Jn);
@@ -510,7 +775,7 @@ struct Builder {
         st.C = G;
         st.aux1 = V;
         st.aux2 = sig;
-        st.no_v = 1;
+        st.no_v = grad ? 0 : 1;
         st.work = K3;
         // left singular side (rows of the Jacobi matrix) and right side
         st.out1 = tall ? Ab : Bb;
@@ -521,7 +786,7 @@ struct Builder {
         add(st);
       }
       // right factor V_k sigma^1/2 = G0^T U_k sigma^-1/2 = G0^T K3 into rows 0..Jn-1 of out2
-      {
+      if (!grad) {
         PView G0T = M0c, K3v = K3, R = tall ? Bb : Ab;
         G0T.rs = Jm;
         G0T.cs = 1;
@@ -548,9 +813,16 @@ struct Builder {
     }
     // the paper's absorb contractions: (D_A x r_A)(r_A x k) and (k x r_B)(r_B x D_B)
     plan->gemm_flops += 2.0 * DA * rA * (double)kk + 2.0 * kk * rB * (double)DB;
-    rescale(na);
-    rescale(nbv);
-    for (auto& t : trel) arena.release(t.first, t.second);
+    const int slot_a = rescale(na), slot_b = rescale(nbv);
+    if (grad) {
+      const int my_op = op_index;
+      bwd.push_back([=, this]() {
+        op_index = my_op;
+        compress_adjoint(ia, ib, ia0, ib0, A, B, DA, DB, dab, rA, rB, kk, tall, Jm, Jn, workA, workB, RA, LB, G, V,
+                         sig, na, nbv, slot_a, slot_b);
+      });
+    }
+    for (auto& t : trel) rel(t.first, t.second);
     for (int t : tmps) release_value(t);
     release_value(ia0);
     release_value(ib0);
@@ -593,7 +865,7 @@ std::string validate_tree(const Structure& s, const std::vector<int32_t>& ops, i
 }
 
 std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int n_inputs, int chi,
-                       int prec, Plan* out) {
+                       int prec, Plan* out, bool grad) {
   std::string err = validate_tree(s, ops, n_inputs);
   if (!err.empty()) return err;
   if (chi < 1) return "chi must be >= 1";
@@ -602,6 +874,10 @@ std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int 
   out->prec = prec;
   Builder bld{s, chi, out};
   bld.dim = s.bond_dims;
+  bld.grad = grad;
+  bld.keep = grad;
+  out->grad = grad;
+  out->in_total = s.in_total;
   const int nt = (int)s.bonds.size();
   for (int t = 0; t < nt; ++t) {
     Value v;
@@ -627,11 +903,23 @@ std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int 
   const Value& root = bld.vals[bld.cur.begin()->second];
   if (root.size != 1) return "final tensor has open bonds";
   out->final_scalar = bld.base_view(root);
-  out->arena_units = bld.arena.peak();
   Step fin;
   fin.kind = ST_FINAL;
   fin.C = out->final_scalar;
   out->steps.push_back(fin);
+  if (grad) {
+    // reverse pass: d ln|x| / dx = 1 / x at the root, then every op backwards
+    bld.keep = false;
+    bld.in_bwd = true;
+    Step fg;
+    fg.kind = ST_FINAL_GRAD;
+    fg.C = out->final_scalar;
+    fg.out1 = bld.gview(bld.cur.begin()->second);
+    fg.op_index = (int)nops;
+    out->steps.push_back(fg);
+    for (size_t r = bld.bwd.size(); r-- > 0;) bld.bwd[r]();
+  }
+  out->arena_units = bld.arena.peak();
   return "";
 }
 

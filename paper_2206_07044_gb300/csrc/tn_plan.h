@@ -10,7 +10,8 @@
 namespace tnp {
 
 // Which device buffer a view points into.
-enum BufKind : int { BUF_ARENA = 0, BUF_INPUT = 1 };
+enum BufKind : int { BUF_ARENA = 0, BUF_INPUT = 1, BUF_GIN = 2 };  // GIN: adjoints of the inputs,
+                                                                    // laid out like the input block
 
 // A 2-D strided view of one instance's matrix: element (r, c) at
 // base + r*rs + c*cs; per-instance stride bs.  For the arena, base is
@@ -20,6 +21,7 @@ struct PView {
   int64_t off = 0;  // arena: per-instance-unit offset; input: element offset
   int64_t rs = 0, cs = 0;
   int64_t bs = 0;   // per-instance stride (arena: the buffer's per-instance size)
+  int64_t eo = 0;   // element offset inside each instance's block (sub-matrix views)
 };
 
 enum StepKind : int {
@@ -36,8 +38,15 @@ enum StepKind : int {
   ST_COPY = 10,       // dst <- src, count elements per instance (same per-instance stride)
   ST_APPLYQ = 11,     // C (m x k col-major) <- Q C, Q the reflectors in `work` (m x n QR)
   ST_GEMM_TC = 12,    // C = alpha A B on tcgen05 tensor cores (tc_mode), FP64 in and out, `work` scratch
+  // reverse pass
+  ST_SCALE_POW2 = 13,   // C (count elements) *= 2^-e, e from rescale tape slot `slot`
+  ST_FINAL_GRAD = 14,   // out1 = 1 / C (the root scalar)
+  ST_SVD_FACTORS = 15,  // sorted factors of a Jacobi SVD (C = G, aux1 = V, aux2 = sigma; flag = tall)
+                        //   -> out1 = U, out2 = W, work = s, A = Us, B = Ws
+  ST_SVD_ADJ_CORE = 16, // C (n x n) from A = P, B = Q (n x k), work = s
+  ST_COPY2D = 17,       // C view <- A view (m x n)
 };
-constexpr int kNumStepKinds = 13;
+constexpr int kNumStepKinds = 18;
 
 struct Step {
   int kind = 0;
@@ -60,6 +69,8 @@ struct Step {
   int64_t work_bytes = 0;  // tensor-core GEMM: scratch bytes for the whole batch (per instance x batch)
   double jac_tol = 1e-9;   // FP64 Jacobi: relative off-diagonal below which a pair counts as converged
   int no_v = 0;            // FP64 Jacobi / select: V not accumulated; select writes K3 into `work`
+  int flag = 0;            // apply_q: 1 = apply Q^T; svd factors: 1 = the Jacobi matrix is M (else M^T)
+  int slot = -1;           // rescale: tape slot receiving the exponents (reverse-pass plans)
   int lane = 0;            // 1: may run on the side stream, concurrently with the main stream
   int join = 0;            // 1: the main stream waits for the side stream before this step
   // accounting
@@ -87,6 +98,12 @@ struct Plan {
   double gemm_flops = 0, qr_flops = 0, svd_flops = 0, permute_bytes = 0;
   int64_t max_jacobi_n = 0;
   PView final_scalar;
+  // reverse-pass plans: the forward keeps every operand, then the steps of the
+  // reverse pass follow ST_FINAL; the adjoints of the inputs land in BUF_GIN
+  bool grad = false;
+  int n_slots = 0;           // rescale tape slots (ints per instance)
+  int64_t in_total = 0;      // elements of the input block per instance
+  double bwd_flops = 0;      // GEMM flops of the reverse pass
   uint64_t serial = 0;       // set by the owner; distinct per plan built (keys captured graphs)
 };
 
@@ -99,8 +116,9 @@ struct Structure {
 };
 
 // ops: rows {kind, i, j, k}.  Returns "" on success, else an error message.
+// grad: also emit the reverse pass (d log|Z| / d inputs).
 std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int n_inputs, int chi,
-                       int prec, Plan* out);
+                       int prec, Plan* out, bool grad = false);
 
 // Validate a tree against a structure without chi (ids, order, final scalar).
 std::string validate_tree(const Structure& s, const std::vector<int32_t>& ops, int n_inputs);

@@ -61,6 +61,8 @@ SIGNATURES = {
     "tn_load_tree_file": (C.c_int, [C.c_void_p, C.c_int, C.c_char_p, C.POINTER(C.c_int)]),
     "tn_contract_approx": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
                                      C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "tn_grad": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_double),
+                          C.POINTER(C.c_int), C.POINTER(C.c_void_p), C.c_int]),
     "tn_plan_stats_get": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(PlanStats)]),
     "tn_debug_tensor": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_int, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int32),
@@ -111,6 +113,8 @@ class Context:
             raise TNError(rc, f"tn_create(device={device}) failed (no CUDA device?)")
         self._h = h
         self.device = device
+        self._shapes: Dict[int, List[Tuple[int, ...]]] = {}   # net id -> tensor shapes
+        self._inst_net: Dict[int, int] = {}                   # instance id -> net id
         if stream is not None:
             self.set_stream(stream)
 
@@ -145,6 +149,7 @@ class Context:
                            ptrs)
         out = C.c_int()
         self._check(self._L.tn_load_network(self._h, C.byref(desc), C.byref(out)))
+        self._shapes[out.value] = [tuple(int(net.bond_dims[b]) for b in bl) for bl in net.bonds]
         return out.value
 
     def load_network_file(self, path: str) -> int:
@@ -181,6 +186,7 @@ class Context:
                         ops.ctypes.data_as(C.POINTER(C.c_int32)) if ops.size else None)
         out = C.c_int()
         self._check(self._L.tn_load_tree(self._h, int(net_id), C.byref(desc), C.byref(out)))
+        self._inst_net[out.value] = int(net_id)
         return out.value
 
     def load_tree_file(self, net_id: int, path: str) -> int:
@@ -199,6 +205,53 @@ class Context:
                                                logz.ctypes.data_as(C.POINTER(C.c_double)),
                                                sign.ctypes.data_as(C.POINTER(C.c_int))))
         return logz, sign
+
+    def shapes(self, inst_id: int) -> List[Tuple[int, ...]]:
+        """Tensor shapes of an instance's network (networks loaded from arrays)."""
+        return self._shapes[self._inst_net[inst_id]]
+
+    def grad(self, inst_ids: Sequence[int], chi: int, prec="f64", out=None):
+        """(log|Z|, sign, gradients): d log|Z| / d T_v for every input tensor, on the GPU.
+
+        Without ``out``, returns per instance a list of host arrays shaped like the
+        inputs.  ``out``: one buffer per instance (numpy arrays, or CUDA tensors
+        passed by device pointer) of sum_t |T_t| float64 values, filled packed.
+        """
+        ids = np.ascontiguousarray(list(inst_ids), dtype=np.int32)
+        n = len(ids)
+        logz = np.zeros(n, dtype=np.float64)
+        sign = np.zeros(n, dtype=np.int32)
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        on_device = False
+        if out is None:
+            shapes = [self.shapes(int(i)) for i in ids]
+            out = [np.zeros(sum(int(np.prod(s, dtype=np.int64)) for s in sh), dtype=np.float64) for sh in shapes]
+        ptrs = []
+        for o in out:
+            if hasattr(o, "data_ptr"):
+                on_device = o.device.type == "cuda"
+                if not (o.is_contiguous() and str(o.dtype) == "torch.float64"):
+                    raise ValueError("gradient buffers must be contiguous float64")
+                ptrs.append(int(o.data_ptr()))
+            else:
+                if o.dtype != np.float64 or not o.flags["C_CONTIGUOUS"]:
+                    raise ValueError("gradient buffers must be contiguous float64")
+                ptrs.append(o.ctypes.data)
+        arr = (C.c_void_p * n)(*ptrs)
+        self._check(self._L.tn_grad(self._h, n, ids.ctypes.data_as(C.POINTER(C.c_int)), int(chi), p,
+                                    logz.ctypes.data_as(C.POINTER(C.c_double)),
+                                    sign.ctypes.data_as(C.POINTER(C.c_int)), arr, 1 if on_device else 0))
+        if on_device or hasattr(out[0], "data_ptr"):
+            return logz, sign, out
+        grads = []
+        for i, o in zip(ids, out):
+            parts, off = [], 0
+            for s in self.shapes(int(i)):
+                sz = int(np.prod(s, dtype=np.int64))
+                parts.append(o[off:off + sz].reshape(s))
+                off += sz
+            grads.append(parts)
+        return logz, sign, grads
 
     def debug_tensor(self, inst_ids: Sequence[int], which: int, chi: int, stop_op: int, tensor_id: int,
                      prec="f64") -> Tuple[np.ndarray, List[int]]:
