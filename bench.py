@@ -379,7 +379,11 @@ def run_ours(args):
         "vs_plain_fp64_unbatched": (value / world) / plain["value"] if plain else None,
         "forms": forms,
         "roofline": roof,
-        "kernel_share": {n_: round(t_ / prof_ms, 4) for n_, _, t_ in fam_sorted},
+        "kernel_share": {n_: round(t_ / prof_ms, 4) for n_, _, t_ in fam_sorted if not n_.startswith("sweeps:")},
+        "jacobi_sweeps_per_matrix": {
+            prec_: round(dict((a, b) for a, b, _ in fam).get("sweeps:jacobi_" + prec_, 0) /
+                         max(1, dict((a, b) for a, b, _ in fam).get("jacobi_" + prec_, 0) * INSTANCES), 3)
+            for prec_ in ("f32", "f64")},
         "profiled_pass_ms": prof_ms,
         "graph": graph,
         "clocks": clk.summary(),

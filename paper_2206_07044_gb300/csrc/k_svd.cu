@@ -82,6 +82,7 @@ struct JacArgs {
   T sig_tol;        // ... and the pair is not yet converged iff |gamma| > sig_tol * sqrt(alpha beta)
   T floor_rel;      // columns with |g| <= floor_rel * |G|_F are left alone
   T floor2;         // (set in the kernel) floor_rel^2 * |G|_F^2
+  T tol2, sig_tol2; // (set in the kernel) tol^2, sig_tol^2
   unsigned long long* sweep_ctr;  // optional: total sweeps run, summed over matrices
 };
 
@@ -159,16 +160,22 @@ __device__ __forceinline__ bool jacobi_pair(T* gx, T* gy, T* vx, T* vy, int m, i
   T ga = T(0);
   for (int r = lane; r < m; r += 32) ga = fma(ld<T, kGlobal>(gx + r), ld<T, kGlobal>(gy + r), ga);
   ga = warp_sum(ga);
-  const T rel = fabs(ga) / (sqrt(al) * sqrt(be));
-  if (!(rel > p.tol)) return false;
-  const T zeta = (be - al) / (T(2) * ga);
-  const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-  const T c = T(1) / sqrt(T(1) + t * t);
+  // The tests |gamma| > tol sqrt(alpha beta) are made on squares (no square
+  // root or division), and the rotation takes one square root, one division
+  // and one reciprocal square root: every lane of the warp evaluates these
+  // scalars, and on the FP64 pipe they cost more than the column updates.
+  //   t = tan(theta) = sgn(d) h / (|d| + sqrt(d^2 + h^2)),  d = beta - alpha, h = 2 gamma
+  // (the smaller root of t^2 + 2 (d / h) t - 1 = 0), c = 1 / sqrt(1 + t^2), s = c t.
+  const T g2 = ga * ga, ab = al * be;
+  if (!(g2 > p.tol2 * ab)) return false;
+  const T d = be - al, h = T(2) * ga;
+  const T t = (d >= T(0) ? h : -h) / (fabs(d) + sqrt(d * d + h * h));
+  const T c = rsqrt(T(1) + t * t);
   const T s = c * t;
   __syncwarp();
   rot_cols_norms<T, kGlobal>(gx, gy, m, c, s, lane, al, be);
   if (vx) rot_cols_g<T, kGlobal>(vx, vy, n, c, s, lane);
-  return rel > p.sig_tol;
+  return g2 > p.sig_tol2 * ab;
 }
 
 template <typename T>
@@ -186,6 +193,8 @@ __global__ void __launch_bounds__(kThreads) block_jacobi_kernel(JacArgs<T> p) {
   T* V = has_v ? p.V + (int64_t)bidx * p.v_bs : nullptr;
   int* cnt = p.ws + kWsInts * bidx;
   p.floor2 = p.floor_rel * p.floor_rel * cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
+  p.tol2 = p.tol * p.tol;
+  p.sig_tol2 = p.sig_tol * p.sig_tol;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Gs = reinterpret_cast<T*>(smem_raw);                  // 2b columns of length m
@@ -324,6 +333,8 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
   T* V = p.V ? p.V + (int64_t)bidx * p.v_bs : nullptr;
   int* cnt = p.ws + kWsInts * bidx;
   p.floor2 = p.floor_rel * p.floor_rel * cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
+  p.tol2 = p.tol * p.tol;
+  p.sig_tol2 = p.sig_tol * p.sig_tol;
   const int np = n + (n & 1);
   const int gw = rank * nwarps + warp, nw = P * nwarps;
   if (V && p.init_v) {
@@ -536,7 +547,7 @@ cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64
                            DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr) {
   // a preconditioner: running out of sweeps is not an error (the FP64 stage decides)
   JacArgs<float> a{m, n, G, g_bs, V, v_bs, nullptr, 0, ws, nullptr, 1, 60,
-                   4.0f * (float)m * FLT_EPSILON, 3e-4f, 1e-6f, 0.0f, sweep_ctr};
+                   4.0f * (float)m * FLT_EPSILON, 3e-4f, 1e-6f, 0.0f, 0.0f, 0.0f, sweep_ctr};
   return launch_jacobi(a, batch, s);
 }
 
@@ -548,7 +559,7 @@ cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int
   // never keep the sweep loop alive
   const double rt = sqrt((double)(m > 16 ? m : 16));
   JacArgs<double> a{m, n, G, g_bs, V, v_bs, sig, sig_bs, ws, st.status, init_v, 60,
-                    rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, sweep_ctr};
+                    rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, 0.0, 0.0, sweep_ctr};
   return launch_jacobi(a, batch, s);
 }
 
