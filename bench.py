@@ -46,6 +46,12 @@ def load_peaks():
 # FP64 ALU peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
+# DRAM bytes (read + write) of one launch of the FP64 polish on 8 cores of 256 x 256,
+# the shape and batch of the bulk of this workload's launches: dram__bytes_read.sum +
+# dram__bytes_write.sum from one Nsight Compute capture of such a launch; to be
+# retaken whenever that kernel changes.
+JACOBI_F64_DRAM_BYTES_PER_LAUNCH = 4.268032e6
+
 
 def build_inputs(rank: int, n_inst: int):
     from tn_inputs import networks as nw
@@ -358,8 +364,11 @@ def run_ours(args):
     if name in algo:
         flops_launch = algo[name] * INSTANCES / max(launches_per_step[name], 1)
         achieved = flops_launch / (avg_ms * 1e-3) / 1e12
+        traffic = JACOBI_F64_DRAM_BYTES_PER_LAUNCH if (name == "jacobi_f64" and INSTANCES == 8) else None
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_note": "DRAM bytes of one 8 x (256 x 256) launch from ncu; the algorithmic "
+                                "read of those cores is 4.19 MB" if traffic else None,
                 "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (unit counts and clock)",
                 "share_of_step": tot_ms / prof_ms,
                 "timing": "CUDA events around each launch of one profiled pass (eager, one stream)"}
