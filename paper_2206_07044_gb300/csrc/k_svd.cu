@@ -44,7 +44,8 @@ namespace cg = cooperative_groups;
 namespace tnk {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;      // pair_jacobi_kernel and the small kernels
+constexpr int kMaxJacThreads = 512; // block_jacobi_kernel: one warp per column of a block, 8..16 warps
 constexpr int kWsInts = 64;   // per-matrix scratch: counters + 16 per-CTA double partials
 
 template <typename T>
@@ -179,7 +180,7 @@ __device__ __forceinline__ bool jacobi_pair(T* gx, T* gy, T* vx, T* vy, int m, i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) block_jacobi_kernel(JacArgs<T> p) {
+__global__ void __launch_bounds__(kMaxJacThreads) block_jacobi_kernel(JacArgs<T> p) {
   cg::cluster_group cl = cg::this_cluster();
   const int P = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -425,16 +426,25 @@ cudaError_t launch_jacobi(const JacArgs<T>& a, int batch, cudaStream_t s) {
     const size_t sm = block_smem<T>(a.m, a.n, q, has_v);
     return sm <= kSmemCap ? sm : (size_t)-1;
   };
-  // a round pairs b = n / 2P columns with b others: b pairs per inner round over 8 warps
+  // a round pairs b = n / 2P columns with b others: b pairs per inner step, one
+  // per warp; the CTA gets b warps (8 at least, 16 at most)
+  auto warps_of = [&](int q) {
+    const int b = (a.n + 2 * q - 1) / (2 * q);
+    return b < 8 ? 8 : (b > kMaxJacThreads / 32 ? kMaxJacThreads / 32 : b);
+  };
+  auto threads_of = [&](int q) { return 32 * warps_of(q); };
   auto imbalance = [&](int q) {
     const int b = (a.n + 2 * q - 1) / (2 * q);
-    const int nw = kThreads / 32;
+    const int nw = warps_of(q);
     return (double)((b + nw - 1) / nw * nw) / b;
   };
-  int P = choose_cluster((const void*)block_jacobi_kernel<T>, kThreads, batch, pmax / 2 > 0 ? pmax / 2 : 1, pmax,
-                         smem_of, imbalance);
+  // The FP64 polish is bound by the SM's FP64 pipe, so a wave counts clusters
+  // whose CTAs each own an SM; the FP32 pass is latency-bound and shares SMs well.
+  const bool fp64 = sizeof(T) == sizeof(double);
+  int P = choose_cluster((const void*)block_jacobi_kernel<T>, batch, pmax / 2 > 0 ? pmax / 2 : 1, pmax, smem_of,
+                         imbalance, threads_of, fp64);
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.blockDim = dim3(P > 0 ? threads_of(P) : kThreads, 1, 1);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

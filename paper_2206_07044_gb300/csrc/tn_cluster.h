@@ -48,18 +48,43 @@ inline int resident_clusters(const void* func, int cluster, int threads, size_t 
   return n;
 }
 
+// Dynamic shared memory that leaves room for one CTA per SM at most (the
+// residency query then counts clusters whose CTAs each own an SM).
+inline size_t one_cta_per_sm_smem(size_t smem) {
+  static size_t half = 0;
+  if (!half) {
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 0;
+    }
+    half = (size_t)per_sm / 2 + 1024;
+  }
+  return smem > half ? smem : half;
+}
+
 // Best P in [lo, hi] for `batch` matrices; smem_of(P) gives the dynamic shared
-// memory of a launch with P CTAs per cluster ((size_t)-1 to skip that P) and
-// imbalance(P) >= 1 the factor by which per-CTA work exceeds an even split.
-// Returns 0 when no P in the range can be placed.
-template <typename SmemFn, typename ImbFn>
-int choose_cluster(const void* func, int threads, int batch, int lo, int hi, SmemFn smem_of, ImbFn imbalance) {
+// memory of a launch with P CTAs per cluster ((size_t)-1 to skip that P),
+// imbalance(P) >= 1 the factor by which per-CTA work exceeds an even split and
+// threads_of(P) the CTA size.  With one_per_sm, waves are counted for clusters
+// whose CTAs each own an SM (for kernels bound by a per-SM pipe, where two CTAs
+// on one SM run at half speed each).  Returns 0 when no P in the range can be
+// placed.
+template <typename SmemFn, typename ImbFn, typename ThrFn>
+int choose_cluster(const void* func, int batch, int lo, int hi, SmemFn smem_of, ImbFn imbalance, ThrFn threads_of,
+                   bool one_per_sm) {
   int best = 0;
   double best_cost = 1e300;
   for (int P = hi; P >= lo; --P) {
     const size_t smem = smem_of(P);
     if (smem == (size_t)-1) continue;
-    const int r = resident_clusters(func, P, threads, smem);
+    const int threads = threads_of(P);
+    int r = resident_clusters(func, P, threads, smem);
+    if (one_per_sm && r > 0) {
+      const int r1 = resident_clusters(func, P, threads, one_cta_per_sm_smem(smem));
+      if (r1 > 0) r = r1;
+    }
     if (r < 1) continue;
     const int waves = (batch + r - 1) / r;
     const double cost = (double)waves / P * imbalance(P);
@@ -69,6 +94,11 @@ int choose_cluster(const void* func, int threads, int batch, int lo, int hi, Sme
     }
   }
   return best;
+}
+
+template <typename SmemFn, typename ImbFn>
+int choose_cluster(const void* func, int threads, int batch, int lo, int hi, SmemFn smem_of, ImbFn imbalance) {
+  return choose_cluster(func, batch, lo, hi, smem_of, imbalance, [threads](int) { return threads; }, false);
 }
 
 }  // namespace tnk
