@@ -51,15 +51,25 @@ inline int resident_clusters(const void* func, int cluster, int threads, size_t 
 // Dynamic shared memory that leaves room for one CTA per SM at most (the
 // residency query then counts clusters whose CTAs each own an SM).
 inline size_t one_cta_per_sm_smem(size_t smem) {
-  static size_t half = 0;
+  static std::mutex mu;
+  static std::map<int, size_t> half_of;  // per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  size_t half = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = half_of.find(dev);
+    if (it != half_of.end()) half = it->second;
+  }
   if (!half) {
-    int dev = 0, per_sm = 0;
-    cudaGetDevice(&dev);
+    int per_sm = 0;
     if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
       cudaGetLastError();
       per_sm = 0;
     }
     half = (size_t)per_sm / 2 + 1024;
+    std::lock_guard<std::mutex> lk(mu);
+    half_of[dev] = half;
   }
   return smem > half ? smem : half;
 }

@@ -381,3 +381,29 @@ def test_planted_truncation_of_smallest_values_is_caught(monkeypatch):
     monkeypatch.setattr(approx.np.linalg, "svd", svd_ascending)
     r = approx.contract(net, tr.boundary_rows(8, 8), 8)
     assert rel(r.logabs, tm) > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# the torch Ising builder (used for d/d beta, d/d J through autograd) against
+# the numpy builder, and its beta-derivative against central differences
+
+
+def test_torch_ising_builder_matches_numpy_and_differentiates():
+    import torch
+    from tn_inputs import torch_ising as ti
+    n, e = nw.cubic_lattice(2, 2, 2)
+    for J0, beta in ((np.ones(len(e)), 0.44), (nw.spin_glass_couplings(len(e), seed=2), 0.7)):
+        sym = bool(np.all(J0 > 0))
+        b = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+        T = ti.ising_tensors(n, e, b, torch.tensor(J0), sym)
+        ref = nw.ising_network(n, e, beta, J0)
+        for t, r in zip(T, ref.data):
+            assert np.allclose(t.detach().numpy(), r, rtol=0, atol=1e-14)
+        # d/d beta of a linear functional of the tensors, against central differences
+        w = [np.random.default_rng(v).normal(size=r.shape) for v, r in enumerate(ref.data)]
+        f = sum((t * torch.from_numpy(wv)).sum() for t, wv in zip(T, w))
+        f.backward()
+        h = 1e-6
+        fp = sum(float(np.sum(wv * r)) for wv, r in zip(w, nw.ising_network(n, e, beta + h, J0).data))
+        fm = sum(float(np.sum(wv * r)) for wv, r in zip(w, nw.ising_network(n, e, beta - h, J0).data))
+        assert abs(float(b.grad) - (fp - fm) / (2 * h)) < 1e-7 * max(1.0, abs(float(b.grad)))
