@@ -401,6 +401,54 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+def run_gemm_check(args):
+    """Contraction-GEMM throughput of each form on one large pairwise contraction.
+
+    Network: A[x, y, e] and B[e, u, v] with |x| = |y| = |u| = |v| = g and
+    |e| = g^2, closed by C[x, u] and D[y, v]; the first tree op is an
+    (g^2 x g^2) x (g^2 x g^2) GEMM (2 g^6 FLOP), the rest is small.  Entries
+    Normal(0, 1).  Prints one JSON line: per form the GEMM kernel's CUDA-event
+    time (gemm_f64 or gemm_tc, the staging kernels of the tensor-core forms
+    included in gemm_tc), its TFLOP/s, and log|Z| relative to the FP64 form.
+    """
+    import numpy as np
+    import torch
+    from paper_2206_07044_gb300 import Context, build
+    from tn_inputs.formats import Network, Tree
+    build.build()
+    g = args.gemm_check
+    E = g * g
+    rng = np.random.default_rng(7)
+    dims = [E, g, g, g, g]                    # bonds: e, x, y, u, v
+    bonds = [[1, 2, 0], [0, 3, 4], [1, 3], [2, 4]]
+    data = [rng.normal(size=(g, g, E)), rng.normal(size=(E, g, g)), rng.normal(size=(g, g)),
+            rng.normal(size=(g, g))]
+    net = Network(dims, bonds, data)
+    tree = Tree(4, [("C", 0, 1, 4), ("C", 4, 2, 5), ("C", 5, 3, 6)])
+    ctx = Context(0, stream=torch.cuda.current_stream())
+    iid = ctx.load_tree(ctx.load_network(net), tree)
+    flop = 2.0 * E * E * E
+    out = {"mode": "gemm_check", "gemm": f"{E} x {E} x {E} (2 g^6 = {flop:.3e} FLOP)", "forms": {}}
+    ref = None
+    peaks = load_peaks()
+    for prec in ("f64", "tf32", "bf16", "tf32x3"):
+        ctx.contract([iid], 1, prec)
+        ctx.profile(True)
+        lz, _ = ctx.contract([iid], 1, prec)
+        fam = {n_: (l_, t_) for n_, l_, t_ in ctx.kernel_times()}
+        ctx.profile(False)
+        key = "gemm_f64" if prec == "f64" else "gemm_tc"
+        # the largest launch dominates: count the family's whole time against the big GEMM's FLOPs
+        ms = fam.get(key, (0, 0.0))[1]
+        if ref is None:
+            ref = float(lz[0])
+        out["forms"][prec] = {"kernel_ms": ms, "tflops": flop / (ms * 1e-3) / 1e12 if ms else None,
+                              "rel_logz_vs_f64": abs(float(lz[0]) - ref) / abs(ref)}
+    out["measured_peaks"] = {k: peaks[k] for k in peaks if "tflops" in k} if isinstance(peaks, dict) else None
+    ctx.close()
+    print(json.dumps(out))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -433,12 +481,16 @@ def main():
     ap.add_argument("--prec", default="f64", choices=["f64", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the unbatched and mixed-form legs")
+    ap.add_argument("--gemm-check", type=int, default=0, metavar="G",
+                    help="instead of the benchmark: throughput of each GEMM form on a (G^2)^3 contraction")
     ap.add_argument("--L", type=int, default=L, help="lattice side (a smaller case for profiling)")
     ap.add_argument("--instances", type=int, default=INSTANCES, help="instances per GPU")
     args = ap.parse_args()
     globals()["L"] = args.L
     globals()["INSTANCES"] = args.instances
-    if args.impl == "reference":
+    if args.gemm_check:
+        run_gemm_check(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
