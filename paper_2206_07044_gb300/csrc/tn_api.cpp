@@ -314,6 +314,18 @@ const tnp::Plan* get_plan(tn_ctx* c, int inst, int chi, int prec, int* rc, bool 
     return nullptr;
   }
   cp.plan.serial = ++c->plan_serial;
+  if (it != c->plans.end()) {
+    // the cached plan of this key is replaced: its captured graphs can never run again
+    const uint64_t old_serial = it->second.plan.serial;
+    for (auto g = c->graphs.begin(); g != c->graphs.end();) {
+      if (g->first.plan_serial == old_serial) {
+        if (g->second.exec) cudaGraphExecDestroy(g->second.exec);
+        g = c->graphs.erase(g);
+      } else {
+        ++g;
+      }
+    }
+  }
   auto res = c->plans.insert_or_assign(key, std::move(cp));
   return &res.first->second.plan;
 }
