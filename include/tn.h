@@ -191,6 +191,23 @@ int tn_contract_approx(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, in
 int tn_grad(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, int prec, double* logabsz_out,
             int* sign_out, double* const* grad_out, int on_device);
 
+/* Diagnostic, needs no context and no GPU: the static schedule that
+ * tn_contract_approx (grad = 0) or tn_grad (grad = 1) would run for this
+ * network structure (the data pointers are not read), tree, chi and form
+ * (schedule expansion, Algorithm 1 with explicit ops), written as one JSON
+ * object: {"arena_units", "n_slots", "in_total", "grad", "in_off": [...],
+ * "steps": [{"kind", "op", "m", "n", "k", "flag", "slot", "no_v", "init_v",
+ * "count", "fbs_src", "fbs_dst", "alpha", "beta", "tc_mode", "A", "B", "C",
+ * "src", "dst", "work", "aux1", "aux2", "out1", "out2", "in_dims", "perm"}]},
+ * each view as [buffer (0 arena, 1 inputs, 2 input adjoints), offset,
+ * row stride, column stride, per-instance stride, element offset]; the step
+ * kinds and buffer layouts are those of the library's executor (arena
+ * buffers at offset * batch + instance * stride).  *need receives the size
+ * including the terminating NUL; buf == NULL queries it.  Errors: TN_EINVAL
+ * (bad arguments, cap too small), TN_ESHAPE / TN_EFORMAT (bad network or tree). */
+int tn_plan_describe(const tn_network_desc* net, const tn_tree_desc* tree, int chi, int prec, int grad, char* buf,
+                     size_t cap, size_t* need);
+
 /* Schedule statistics of one instance at chi (no GPU work). */
 int tn_plan_stats_get(tn_ctx* ctx, int inst_id, int chi, int prec, tn_plan_stats* out);
 

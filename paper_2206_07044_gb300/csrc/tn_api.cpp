@@ -890,6 +890,58 @@ int tn_grad(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, doubl
   return TN_OK;
 }
 
+int tn_plan_describe(const tn_network_desc* d, const tn_tree_desc* t, int chi, int prec, int grad, char* buf,
+                     size_t cap, size_t* need) {
+  if (!d || !t || !need) return TN_EINVAL;
+  if (chi < 1 || prec < TN_F64 || prec > TN_TF32X3 || t->n_ops < 0 || (t->n_ops > 0 && !t->ops)) return TN_EINVAL;
+  tnp::Structure st;
+  int rc = load_structure(nullptr, d->n_bonds, d->bond_dims, d->n_tensors, d->ndims, d->bond_ids, &st);
+  if (rc != TN_OK) return rc;
+  std::vector<int32_t> ops(t->ops, t->ops + 4 * (size_t)t->n_ops);
+  tnp::Plan plan;
+  std::string err;
+  try {
+    err = tnp::build_plan(st, ops, t->n_inputs, chi, prec, &plan, grad != 0);
+  } catch (...) {
+    return TN_ENOMEM;
+  }
+  if (!err.empty()) return TN_EFORMAT;
+  std::ostringstream o;
+  o.precision(17);
+  auto view = [&](const tnp::PView& v) {
+    o << "[" << v.buf << "," << v.off << "," << v.rs << "," << v.cs << "," << v.bs << "," << v.eo << "]";
+  };
+  o << "{\"arena_units\":" << plan.arena_units << ",\"n_slots\":" << plan.n_slots << ",\"in_total\":" << st.in_total
+    << ",\"grad\":" << (plan.grad ? 1 : 0) << ",\"in_off\":[";
+  for (size_t q = 0; q < st.in_off.size(); ++q) o << (q ? "," : "") << st.in_off[q];
+  o << "],\"steps\":[";
+  for (size_t q = 0; q < plan.steps.size(); ++q) {
+    const tnp::Step& x = plan.steps[q];
+    o << (q ? "," : "") << "{\"kind\":" << x.kind << ",\"op\":" << x.op_index << ",\"m\":" << x.m << ",\"n\":" << x.n
+      << ",\"k\":" << x.k << ",\"flag\":" << x.flag << ",\"slot\":" << x.slot << ",\"no_v\":" << x.no_v
+      << ",\"init_v\":" << x.init_v << ",\"count\":" << x.count << ",\"fbs_src\":" << x.fbs_src
+      << ",\"fbs_dst\":" << x.fbs_dst << ",\"alpha\":" << x.alpha << ",\"beta\":" << x.beta << ",\"tc_mode\":" << x.tc_mode;
+    const char* names[] = {"A", "B", "C", "src", "dst", "work", "aux1", "aux2", "out1", "out2"};
+    const tnp::PView* vs[] = {&x.A, &x.B, &x.C, &x.src, &x.dst, &x.work, &x.aux1, &x.aux2, &x.out1, &x.out2};
+    for (int w = 0; w < 10; ++w) {
+      o << ",\"" << names[w] << "\":";
+      view(*vs[w]);
+    }
+    o << ",\"in_dims\":[";
+    for (size_t a = 0; a < x.in_dims.size(); ++a) o << (a ? "," : "") << x.in_dims[a];
+    o << "],\"perm\":[";
+    for (size_t a = 0; a < x.perm.size(); ++a) o << (a ? "," : "") << x.perm[a];
+    o << "]}";
+  }
+  o << "]}";
+  const std::string js = o.str();
+  *need = js.size() + 1;
+  if (!buf) return TN_OK;
+  if (cap < js.size() + 1) return TN_EINVAL;
+  std::memcpy(buf, js.c_str(), js.size() + 1);
+  return TN_OK;
+}
+
 int tn_debug_tensor(tn_ctx* c, int n_inst, const int* inst_ids, int which, int chi, int prec, int stop_op,
                     int tensor_id, double* out, int64_t cap, int32_t* ndim_out, int32_t* bond_ids_out,
                     int64_t* dims_out) {

@@ -63,6 +63,8 @@ SIGNATURES = {
                                      C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "tn_grad": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_double),
                           C.POINTER(C.c_int), C.POINTER(C.c_void_p), C.c_int]),
+    "tn_plan_describe": (C.c_int, [C.POINTER(NetworkDesc), C.POINTER(TreeDesc), C.c_int, C.c_int, C.c_int,
+                                   C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "tn_plan_stats_get": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(PlanStats)]),
     "tn_debug_tensor": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_int, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int32),
@@ -92,6 +94,37 @@ def lib() -> C.CDLL:
             f.argtypes = args
         _LIB = L
     return _LIB
+
+
+def plan_describe(net, tree, chi: int, prec="f64", grad: bool = False) -> dict:
+    """The library's static schedule for (network structure, tree, chi, form) as a dict.
+
+    Needs no context and no GPU (host planning only); see tn_plan_describe in
+    include/tn.h for the fields.
+    """
+    import json
+    L = lib()
+    dims = np.ascontiguousarray(net.bond_dims, dtype=np.int64)
+    ndims = np.array([len(b) for b in net.bonds], dtype=np.int32)
+    ids = np.ascontiguousarray(np.concatenate([np.asarray(b, dtype=np.int32) for b in net.bonds])
+                               if sum(ndims) else np.zeros(1, np.int32), dtype=np.int32)
+    desc = NetworkDesc(len(dims), dims.ctypes.data_as(C.POINTER(C.c_int64)), len(net.bonds),
+                       ndims.ctypes.data_as(C.POINTER(C.c_int32)), ids.ctypes.data_as(C.POINTER(C.c_int32)), None)
+    ops = np.ascontiguousarray(tree.as_int_array(), dtype=np.int32)
+    if ops.size == 0:
+        ops = np.zeros((0, 4), np.int32)
+    tdesc = TreeDesc(int(tree.n_inputs), int(ops.shape[0]), ops.ctypes.data_as(C.POINTER(C.c_int32)) if ops.size else None)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    need = C.c_size_t()
+    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, 1 if grad else 0, None, 0, C.byref(need))
+    if rc != 0:
+        raise TNError(rc, "tn_plan_describe failed")
+    buf = C.create_string_buffer(need.value)
+    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, 1 if grad else 0, buf, need.value,
+                            C.byref(need))
+    if rc != 0:
+        raise TNError(rc, "tn_plan_describe failed")
+    return json.loads(buf.value.decode())
 
 
 def _stream_handle(stream) -> int:
