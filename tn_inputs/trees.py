@@ -247,6 +247,121 @@ class _Sim:
         return True
 
 
+def local_spanning_tree(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], start: Sequence[int],
+                        r: Optional[int] = None, score=None) -> Tuple[List[Tuple[int, int]], List[int]]:
+    """The r-local spanning tree of Algorithm 2 (r = None: unbounded).
+
+    Grows a region from the nodes `start` one node at a time: candidates are
+    (u, v, r_uv) with u in the region, v a neighbour outside it and r_uv its
+    distance from the start region; the best candidate (largest `score(u, v,
+    r_uv, region)`, default: the closest, then the largest connectivity -- the
+    product of the sizes of the bonds v shares with the region) is popped,
+    and v, if still outside and within distance r, joins the region with the
+    pair (u, v) appended to the tree.  Returns (ordered pairs, region).
+    """
+    n = len(net_bonds)
+    owner: Dict[int, List[int]] = {}
+    for t, bl in enumerate(net_bonds):
+        for b in bl:
+            owner.setdefault(b, []).append(t)
+    nbr: List[Dict[int, float]] = [dict() for _ in range(n)]   # neighbour -> log2 shared size
+    for t, bl in enumerate(net_bonds):
+        for b in bl:
+            for o in owner[b]:
+                if o != t:
+                    nbr[t][o] = nbr[t].get(o, 0.0) + math.log2(bond_dims[b])
+    region = set(start)
+    order = list(start)
+
+    def connectivity(v):
+        return sum(w for o, w in nbr[v].items() if o in region)
+
+    if score is None:
+        def score(u, v, ruv, reg):
+            return (-ruv, connectivity(v), -v)
+
+    cands: Dict[Tuple[int, int], int] = {}
+    for u in start:
+        for v in nbr[u]:
+            if v not in region:
+                cands[(u, v)] = 1
+    tau: List[Tuple[int, int]] = []
+    while cands:
+        (u, v), ruv = max(cands.items(), key=lambda kv: score(kv[0][0], kv[0][1], kv[1], region))
+        del cands[(u, v)]
+        if v in region or (r is not None and ruv > r):
+            continue
+        region.add(v)
+        order.append(v)
+        tau.append((u, v))
+        for w in nbr[v]:
+            if w not in region and (v, w) not in cands:
+                cands[(v, w)] = ruv + 1
+    return tau, order
+
+
+def span(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], policy: str = "early",
+         start: str = "central", priority: Sequence[str] = ("distance", "connectivity", "ndim", "centrality"),
+         signs: Optional[Dict[str, float]] = None, temperature: float = 0.0, seed: int = 0) -> Tree:
+    """Span tree builder (SI "Span"): a spanning tree grown from one node by
+    Algorithm 2 with r unbounded, contracted leaves inwards.
+
+    The start node has the highest (start="central") or lowest ("peripheral")
+    centrality.  Candidates (u, v) are ranked by the features in `priority`
+    order (lexicographically), each multiplied by its sign (default: prefer
+    close, well connected, low-dimensional, central nodes):
+      distance     -- v's distance from the start node,
+      connectivity -- log2 of the product of the bond sizes v shares with the region,
+      ndim         -- number of bonds of v,
+      centrality   -- v's centrality in [0, 1],
+    with `temperature` times Gumbel noise added to the first feature.  The
+    spanning tree's ordered pairs, reversed, are the contractions (each leaf
+    into its parent), with S ops placed by `policy` as in from_pairs.
+    """
+    n = len(net_bonds)
+    sg = {"distance": -1.0, "connectivity": 1.0, "ndim": -1.0, "centrality": 1.0}
+    sg.update(signs or {})
+    owner: Dict[int, List[int]] = {}
+    for t, bl in enumerate(net_bonds):
+        for b in bl:
+            owner.setdefault(b, []).append(t)
+    adj = [sorted(set(o for b in net_bonds[v] for o in owner[b] if o != v)) for v in range(n)]
+    cent = centrality(n, adj)
+    s0 = int(np.argmax(cent)) if start == "central" else int(np.argmin(cent))
+    rng = np.random.default_rng(seed)
+    noise: Dict[Tuple[int, int], float] = {}
+    shared: List[Dict[int, float]] = [dict() for _ in range(n)]
+    for t, bl in enumerate(net_bonds):
+        for b in bl:
+            for o in owner[b]:
+                if o != t:
+                    shared[t][o] = shared[t].get(o, 0.0) + math.log2(bond_dims[b])
+
+    def score(u, v, ruv, region):
+        feats = {"distance": float(ruv),
+                 "connectivity": sum(w for o, w in shared[v].items() if o in region),
+                 "ndim": float(len(net_bonds[v])),
+                 "centrality": float(cent[v])}
+        key = [sg[f] * feats[f] for f in priority]
+        if temperature > 0.0:
+            if (u, v) not in noise:
+                noise[(u, v)] = float(rng.gumbel())
+            key[0] += temperature * noise[(u, v)]
+        return tuple(key) + (-v,)
+
+    tau, order = local_spanning_tree(net_bonds, bond_dims, [s0], None, score)
+    if len(order) != n:
+        raise ValueError("span: the network is not connected")
+    cur = {v: v for v in range(n)}
+    nxt = n
+    pairs: List[Tuple[int, int]] = []
+    for u, v in reversed(tau):
+        pairs.append((cur[u], cur[v]))
+        cur[u] = nxt
+        nxt += 1
+    return from_pairs(net_bonds, pairs, policy)
+
+
 def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int,
            seed: int = 0, temperature: float = 0.0, w_new: float = 1.0, w_old: float = 0.0,
            w_inputs: float = -1.0, w_subgraph: float = 0.0, w_centrality: float = 0.0,
@@ -389,3 +504,49 @@ def trace_cost(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], tre
     return {"contract": cost_c, "qr": cost_qr, "svd": cost_svd,
             "total": cost_c + cost_qr + cost_svd, "peak": peak, "wmax": wmax,
             "compressions": n_comp}
+
+
+# ---------------------------------------------------------------------------
+# hyper-optimization loop (Algorithm 3) by random search
+
+SPAN_FEATURES = ("distance", "connectivity", "ndim", "centrality")
+
+
+def hyper_search(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int, n_trials: int = 64,
+                 seed: int = 0, builder: str = "span", objective: str = "total"):
+    """Sample builder hyper-parameters, build a tree, score it with the cost
+    tracer, keep the best (Algorithm 3 with random sampling in place of a
+    Bayesian optimizer).
+
+    builder "span": the feature priority order, the signs, the start node
+    (central / peripheral), a temperature in {0, 0.5, 2} and the compression
+    policy (early / late).  builder "greedy": the score weights, the
+    temperature and chi_greedy.  objective: a key of trace_cost's result
+    ("total" = the SI's cost C, "peak" = largest intermediate, ...).
+    Returns (best tree, its parameters, its objective value, [objective of each trial]).
+    """
+    rng = np.random.default_rng(seed)
+    best = (None, None, math.inf)
+    hist: List[float] = []
+    for trial in range(n_trials):
+        if builder == "span":
+            params = dict(policy=str(rng.choice(["early", "late"])),
+                          start=str(rng.choice(["central", "peripheral"])),
+                          priority=tuple(str(x) for x in rng.permutation(SPAN_FEATURES)),
+                          signs={f: float(rng.choice([-1.0, 1.0])) for f in SPAN_FEATURES},
+                          temperature=float(rng.choice([0.0, 0.0, 0.5, 2.0])), seed=trial)
+            tree = span(net_bonds, bond_dims, **params)
+        elif builder == "greedy":
+            params = dict(seed=trial, temperature=float(rng.choice([0.0, 0.1, 0.5])),
+                          w_new=float(rng.uniform(0.5, 1.5)), w_old=float(rng.uniform(-0.5, 0.5)),
+                          w_inputs=float(rng.uniform(-1.5, 0.0)), w_subgraph=float(rng.uniform(-0.2, 0.2)),
+                          w_centrality=float(rng.uniform(-1.0, 1.0)),
+                          chi_greedy=int(rng.choice([chi, 2 * chi, max(1, chi // 2)])))
+            tree = greedy(net_bonds, bond_dims, chi, **params)
+        else:
+            raise ValueError(builder)
+        cost = float(trace_cost(net_bonds, bond_dims, tree, chi)[objective])
+        hist.append(cost)
+        if cost < best[2]:
+            best = (tree, params, cost)
+    return best[0], best[1], best[2], hist
