@@ -182,8 +182,10 @@ int tn_contract_approx(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, in
  * gradients of the input tensors packed in network order, each row-major over
  * its listed bonds (the layout the network was loaded in); host pointers when
  * on_device == 0, device pointers on the context's device otherwise.
- * logabsz_out / sign_out as for tn_contract_approx.  Device memory: every
- * intermediate of the forward pass stays allocated until the call returns.
+ * logabsz_out / sign_out as for tn_contract_approx.  Device memory: by
+ * default every intermediate of the forward pass stays allocated until the
+ * call returns; when that tape would exceed half the free device memory the
+ * pass is checkpointed instead (see tn_set_grad_segments).
  * Errors: TN_EINVAL (bad ids, NULL pointers), TN_ENONFINITE when some Z == 0
  * (log|Z| has no gradient there; the other instances' outputs are written),
  * TN_ENOMEM, TN_ENOCONV, TN_ETIMEOUT, TN_ECUDA as for tn_contract_approx.
@@ -191,11 +193,25 @@ int tn_contract_approx(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, in
 int tn_grad(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, int prec, double* logabsz_out,
             int* sign_out, double* const* grad_out, int on_device);
 
+/* Checkpointing of tn_grad's tape.  segments = k >= 2: the forward pass
+ * copies the live tensors at the start of each of k segments of the tree's
+ * ops (equal op counts) and keeps nothing else; the reverse pass then, for
+ * each segment from the last, recomputes that segment from its checkpoint
+ * with every operand kept, runs its reverse steps and frees its tape, so the
+ * device holds the checkpoints plus one segment's tape (about 1/k of the
+ * whole, at the price of one more forward pass).  Results equal the
+ * one-tape pass (the recomputation repeats the same kernels on the same
+ * data).  segments = 1: one tape of the whole pass.  segments = 0 (default):
+ * one tape if it fits in half the free device memory, else ceil(sqrt(ops))
+ * segments.  Errors: TN_EINVAL for segments < 0. */
+int tn_set_grad_segments(tn_ctx* ctx, int segments);
+
 /* Diagnostic, needs no context and no GPU: the static schedule that
- * tn_contract_approx (grad = 0) or tn_grad (grad = 1) would run for this
+ * tn_contract_approx (grad = 0) or tn_grad (grad = 1; grad = k >= 2: with k
+ * checkpointed segments) would run for this
  * network structure (the data pointers are not read), tree, chi and form
  * (schedule expansion, Algorithm 1 with explicit ops), written as one JSON
- * object: {"arena_units", "n_slots", "in_total", "grad", "in_off": [...],
+ * object: {"arena_units", "n_slots", "in_total", "grad", "segments", "in_off": [...],
  * "steps": [{"kind", "op", "m", "n", "k", "flag", "slot", "no_v", "init_v",
  * "count", "fbs_src", "fbs_dst", "alpha", "beta", "tc_mode", "A", "B", "C",
  * "src", "dst", "work", "aux1", "aux2", "out1", "out2", "in_dims", "perm"}]},

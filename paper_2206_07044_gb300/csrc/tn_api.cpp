@@ -45,7 +45,7 @@ struct InstRec {
 struct PlanKey {
   uint64_t hash;
   int chi, prec;
-  int grad;  // 1: the plan also runs the reverse pass
+  int grad;  // 0: forward only; k >= 1: with the reverse pass, checkpointed in k segments
   bool operator<(const PlanKey& o) const {
     return std::tie(hash, chi, prec, grad) < std::tie(o.hash, o.chi, o.prec, o.grad);
   }
@@ -109,6 +109,7 @@ struct tn_ctx {
   // CUDA graphs: a schedule runs eagerly on its first call (warming every launch
   // configuration), is captured on the second and replayed from then on
   int graph_mode = 1;
+  int grad_segments = 0;  // tn_grad: 0 = choose from free device memory, k >= 1 = k segments
   uint64_t plan_serial = 0;
   uint64_t buf_gen = 0;  // bumped whenever a buffer a captured graph points into moves
   cudaStream_t cap = nullptr;
@@ -301,14 +302,16 @@ int ensure_scratch(tn_ctx* c, int batch) {
   return TN_OK;
 }
 
-const tnp::Plan* get_plan(tn_ctx* c, int inst, int chi, int prec, int* rc, bool grad = false) {
-  PlanKey key{c->insts[inst].hash, chi, prec, grad ? 1 : 0};
+// grad: 0 forward only, k >= 1 with the reverse pass in k checkpointed segments
+const tnp::Plan* get_plan(tn_ctx* c, int inst, int chi, int prec, int* rc, int grad = 0) {
+  PlanKey key{c->insts[inst].hash, chi, prec, grad};
   auto it = c->plans.find(key);
   if (it != c->plans.end() && same_group(c, it->second.inst_proto, inst)) return &it->second.plan;
   CachedPlan cp;
   cp.inst_proto = inst;
   const InstRec& r = c->insts[inst];
-  std::string err = tnp::build_plan(c->nets[r.net].st, r.ops, r.n_inputs, chi, prec, &cp.plan, grad);
+  std::string err = tnp::build_plan(c->nets[r.net].st, r.ops, r.n_inputs, chi, prec, &cp.plan, grad > 0,
+                                    grad > 0 ? grad : 1);
   if (!err.empty()) {
     *rc = fail(c, TN_EFORMAT, "plan: " + err);
     return nullptr;
@@ -858,8 +861,24 @@ int tn_grad(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, doubl
         done[r] = true;
       }
     int rc = TN_OK;
-    const tnp::Plan* plan = get_plan(c, inst_ids[q], chi, prec, &rc, true);
+    int segs = c->grad_segments > 0 ? c->grad_segments : 1;
+    const tnp::Plan* plan = get_plan(c, inst_ids[q], chi, prec, &rc, segs);
     if (!plan) return rc;
+    if (c->grad_segments == 0) {
+      // the whole tape does not fit in half the free device memory: checkpoint
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+      }
+      const double need = 8.0 * (double)plan->arena_units * (double)members.size();
+      const size_t nops = c->insts[inst_ids[q]].ops.size() / 4;
+      if (free_b && need > 0.5 * (double)free_b && nops > 1) {
+        segs = (int)std::ceil(std::sqrt((double)nops));
+        plan = get_plan(c, inst_ids[q], chi, prec, &rc, segs);
+        if (!plan) return rc;
+      }
+    }
     std::vector<double> lg(members.size());
     std::vector<int> sg(members.size());
     rc = run_group(c, *plan, members, lg.data(), sg.data());
@@ -890,6 +909,12 @@ int tn_grad(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, doubl
   return TN_OK;
 }
 
+int tn_set_grad_segments(tn_ctx* c, int segments) {
+  if (!c || segments < 0) return fail(c, TN_EINVAL, "segments must be >= 0");
+  c->grad_segments = segments;
+  return TN_OK;
+}
+
 int tn_plan_describe(const tn_network_desc* d, const tn_tree_desc* t, int chi, int prec, int grad, char* buf,
                      size_t cap, size_t* need) {
   if (!d || !t || !need) return TN_EINVAL;
@@ -901,7 +926,7 @@ int tn_plan_describe(const tn_network_desc* d, const tn_tree_desc* t, int chi, i
   tnp::Plan plan;
   std::string err;
   try {
-    err = tnp::build_plan(st, ops, t->n_inputs, chi, prec, &plan, grad != 0);
+    err = tnp::build_plan(st, ops, t->n_inputs, chi, prec, &plan, grad != 0, grad > 1 ? grad : 1);
   } catch (...) {
     return TN_ENOMEM;
   }
@@ -912,7 +937,7 @@ int tn_plan_describe(const tn_network_desc* d, const tn_tree_desc* t, int chi, i
     o << "[" << v.buf << "," << v.off << "," << v.rs << "," << v.cs << "," << v.bs << "," << v.eo << "]";
   };
   o << "{\"arena_units\":" << plan.arena_units << ",\"n_slots\":" << plan.n_slots << ",\"in_total\":" << st.in_total
-    << ",\"grad\":" << (plan.grad ? 1 : 0) << ",\"in_off\":[";
+    << ",\"grad\":" << (plan.grad ? 1 : 0) << ",\"segments\":" << plan.segments << ",\"in_off\":[";
   for (size_t q = 0; q < st.in_off.size(); ++q) o << (q ? "," : "") << st.in_off[q];
   o << "],\"steps\":[";
   for (size_t q = 0; q < plan.steps.size(); ++q) {

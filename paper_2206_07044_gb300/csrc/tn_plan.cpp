@@ -128,6 +128,8 @@ struct Builder {
   bool grad = false;
   bool keep = false;
   bool in_bwd = false;
+  bool keep_v = false;   // gradient plans: the FP64 Jacobi keeps V (in every pass, so all passes agree)
+  std::vector<std::pair<int64_t, int64_t>>* rec_alloc = nullptr;  // records allocations (segment tapes)
   std::vector<std::function<void()>> bwd;
   std::unordered_map<int, PView> gv;  // value index -> buffer of its adjoint
 
@@ -148,6 +150,7 @@ struct Builder {
     v.size = prod_dims(v.bonds, dim);
     v.buf = BUF_ARENA;
     v.off = arena.alloc(v.size);
+    if (rec_alloc) rec_alloc->push_back({v.off, v.size});
     v.bs = round_up(std::max<int64_t>(v.size, 1));
     vals.push_back(v);
     return (int)vals.size() - 1;
@@ -156,6 +159,7 @@ struct Builder {
     PView p;
     p.buf = BUF_ARENA;
     p.off = arena.alloc(size);
+    if (rec_alloc) rec_alloc->push_back({p.off, size});
     p.bs = round_up(std::max<int64_t>(size, 1));
     *off_out = p.off;
     return p;
@@ -742,7 +746,7 @@ struct Builder {
       st.init_v = 0;
       // V_k is recovered after the sweeps from M^T U_k (a GEMM), see below; the
       // reverse pass needs every right vector accurately, so it keeps V
-      st.no_v = grad ? 0 : 1;
+      st.no_v = keep_v ? 0 : 1;
       st.jac_tol = 1e-8;
       st.flops = svd_flops((double)rA, (double)rB);
       st.bytes = 8.0 * (2.0 * Jm * Jn + 2.0 * Jn * Jn);
@@ -775,7 +779,7 @@ struct Builder {
         st.C = G;
         st.aux1 = V;
         st.aux2 = sig;
-        st.no_v = grad ? 0 : 1;
+        st.no_v = keep_v ? 0 : 1;
         st.work = K3;
         // left singular side (rows of the Jacobi matrix) and right side
         st.out1 = tall ? Ab : Bb;
@@ -786,7 +790,7 @@ struct Builder {
         add(st);
       }
       // right factor V_k sigma^1/2 = G0^T U_k sigma^-1/2 = G0^T K3 into rows 0..Jn-1 of out2
-      if (!grad) {
+      if (!keep_v) {
         PView G0T = M0c, K3v = K3, R = tall ? Bb : Ab;
         G0T.rs = Jm;
         G0T.cs = 1;
@@ -864,11 +868,120 @@ std::string validate_tree(const Structure& s, const std::vector<int32_t>& ops, i
   return "";
 }
 
+namespace {
+
+// Gradient plan with checkpointed recomputation.  Forward: the ops run with
+// normal arena reuse and no tape; at the start of every segment each live
+// tensor is copied to a checkpoint buffer.  Reverse, segment by segment from
+// the last: the segment's ops run again from its checkpoints with every
+// operand kept (its tape), the adjoints of the tensors live at its end are
+// taken over from the next segment's checkpoints (or the root), its reverse
+// steps run, and its tape and the next segment's checkpoints are released.
+// The arena then holds the checkpoints plus one segment's tape.
+std::string build_checkpointed(Builder& bld, const std::vector<int32_t>& ops, int segments) {
+  Plan* out = bld.plan;
+  const size_t nops = ops.size() / 4;
+  std::vector<size_t> cut;
+  for (int q = 0; q <= segments; ++q) cut.push_back(nops * (size_t)q / (size_t)segments);
+  // per segment: tensor id -> checkpoint value (inputs are their own checkpoint in segment 0)
+  std::vector<std::map<int, int>> ck(segments);
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> ck_alloc(segments);
+  bld.grad = false;
+  bld.keep = false;
+  for (int sg = 0; sg < segments; ++sg) {
+    for (const auto& tv : bld.cur) {
+      const Value& v = bld.vals[tv.second];
+      if (v.buf == BUF_INPUT || sg == 0) {
+        ck[sg][tv.first] = tv.second;
+        continue;
+      }
+      Value c = v;
+      c.off = bld.arena.alloc(c.size);
+      ck_alloc[sg].push_back({c.off, c.size});
+      bld.vals.push_back(c);
+      const int ci = (int)bld.vals.size() - 1;
+      Step cp;
+      cp.kind = ST_COPY;
+      cp.op_index = (int)cut[sg];
+      cp.src = bld.base_view(v);
+      cp.dst = bld.base_view(c);
+      cp.count = c.size;
+      out->steps.push_back(cp);
+      ck[sg][tv.first] = ci;
+    }
+    for (size_t r = cut[sg]; r < cut[sg + 1]; ++r) {
+      bld.op_index = (int)r;
+      const int kind = ops[4 * r], i = ops[4 * r + 1], j = ops[4 * r + 2], k = ops[4 * r + 3];
+      std::string e = (kind == 0) ? bld.contract(i, j, k) : bld.compress(i, j);
+      if (!e.empty()) return "op " + std::to_string(r) + ": " + e;
+    }
+  }
+  if (bld.cur.size() != 1) return "tree does not end in one tensor";
+  const int root = bld.cur.begin()->second;
+  if (bld.vals[root].size != 1) return "final tensor has open bonds";
+  out->final_scalar = bld.base_view(bld.vals[root]);
+  Step fin;
+  fin.kind = ST_FINAL;
+  fin.C = out->final_scalar;
+  out->steps.push_back(fin);
+  Step fg;
+  fg.kind = ST_FINAL_GRAD;
+  fg.C = out->final_scalar;
+  fg.out1 = bld.gview(root);
+  fg.op_index = (int)nops;
+  out->steps.push_back(fg);
+  const int root_tensor = bld.cur.begin()->first;
+  // adjoints of the tensors live at the end of the segment being processed
+  std::map<int, int> end_adj = {{root_tensor, root}};
+  for (int sg = segments - 1; sg >= 0; --sg) {
+    // recompute the segment from its checkpoints, keeping every operand
+    bld.cur.clear();
+    for (const auto& tv : ck[sg]) bld.cur[tv.first] = tv.second;
+    bld.bwd.clear();
+    bld.grad = true;
+    bld.keep = true;
+    bld.in_bwd = false;
+    std::vector<std::pair<int64_t, int64_t>> tape;
+    bld.rec_alloc = &tape;
+    for (size_t r = cut[sg]; r < cut[sg + 1]; ++r) {
+      bld.op_index = (int)r;
+      const int kind = ops[4 * r], i = ops[4 * r + 1], j = ops[4 * r + 2], k = ops[4 * r + 3];
+      std::string e = (kind == 0) ? bld.contract(i, j, k) : bld.compress(i, j);
+      if (!e.empty()) return "op " + std::to_string(r) + " (recomputed): " + e;
+    }
+    bld.rec_alloc = nullptr;
+    // the adjoint of each tensor live at the segment's end moves onto its recomputed value
+    for (const auto& tv : end_adj) {
+      auto it = bld.cur.find(tv.first);
+      if (it == bld.cur.end()) return "checkpoint bookkeeping: tensor missing at a segment end";
+      const int vi = it->second, src = tv.second;
+      if (vi == src) continue;
+      if (bld.vals[vi].size != bld.vals[src].size) return "checkpoint bookkeeping: size mismatch";
+      auto g = bld.gv.find(src);
+      if (g == bld.gv.end()) return "checkpoint bookkeeping: missing adjoint";
+      bld.gv[vi] = g->second;
+      bld.gv.erase(g);
+    }
+    bld.keep = false;
+    bld.in_bwd = true;
+    for (size_t r = bld.bwd.size(); r-- > 0;) bld.bwd[r]();
+    bld.in_bwd = false;
+    for (auto& a : tape) bld.arena.release(a.first, a.second);
+    if (sg + 1 < segments)
+      for (auto& a : ck_alloc[sg + 1]) bld.arena.release(a.first, a.second);
+    end_adj = ck[sg];
+  }
+  return "";
+}
+
+}  // namespace
+
 std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int n_inputs, int chi,
-                       int prec, Plan* out, bool grad) {
+                       int prec, Plan* out, bool grad, int segments) {
   std::string err = validate_tree(s, ops, n_inputs);
   if (!err.empty()) return err;
   if (chi < 1) return "chi must be >= 1";
+  if (segments < 1) return "segments must be >= 1";
   *out = Plan();
   out->chi = chi;
   out->prec = prec;
@@ -876,6 +989,7 @@ std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int 
   bld.dim = s.bond_dims;
   bld.grad = grad;
   bld.keep = grad;
+  bld.keep_v = grad;
   out->grad = grad;
   out->in_total = s.in_total;
   const int nt = (int)s.bonds.size();
@@ -892,6 +1006,13 @@ std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int 
     bld.record(t, t);
   }
   const size_t nops = ops.size() / 4;
+  if (grad && segments > 1 && nops > 1) {
+    out->segments = segments < (int)nops ? segments : (int)nops;
+    std::string e = build_checkpointed(bld, ops, out->segments);
+    if (!e.empty()) return e;
+    out->arena_units = bld.arena.peak();
+    return "";
+  }
   for (size_t r = 0; r < nops; ++r) {
     bld.op_index = (int)r;
     const int kind = ops[4 * r], i = ops[4 * r + 1], j = ops[4 * r + 2], k = ops[4 * r + 3];

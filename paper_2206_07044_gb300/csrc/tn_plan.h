@@ -102,6 +102,7 @@ struct Plan {
   // reverse pass follow ST_FINAL; the adjoints of the inputs land in BUF_GIN
   bool grad = false;
   int n_slots = 0;           // rescale tape slots (ints per instance)
+  int segments = 1;          // checkpointed segments of the reverse pass (1: one tape of the whole pass)
   int64_t in_total = 0;      // elements of the input block per instance
   double bwd_flops = 0;      // GEMM flops of the reverse pass
   uint64_t serial = 0;       // set by the owner; distinct per plan built (keys captured graphs)
@@ -116,9 +117,11 @@ struct Structure {
 };
 
 // ops: rows {kind, i, j, k}.  Returns "" on success, else an error message.
-// grad: also emit the reverse pass (d log|Z| / d inputs).
+// grad: also emit the reverse pass (d log|Z| / d inputs); segments > 1 (with
+// grad): checkpoint the live tensors at that many segment starts and
+// recompute each segment's operands just before its reverse steps.
 std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int n_inputs, int chi,
-                       int prec, Plan* out, bool grad = false);
+                       int prec, Plan* out, bool grad = false, int segments = 1);
 
 // Validate a tree against a structure without chi (ids, order, final scalar).
 std::string validate_tree(const Structure& s, const std::vector<int32_t>& ops, int n_inputs);

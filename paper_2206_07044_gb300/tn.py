@@ -63,6 +63,7 @@ SIGNATURES = {
                                      C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "tn_grad": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_double),
                           C.POINTER(C.c_int), C.POINTER(C.c_void_p), C.c_int]),
+    "tn_set_grad_segments": (C.c_int, [C.c_void_p, C.c_int]),
     "tn_plan_describe": (C.c_int, [C.POINTER(NetworkDesc), C.POINTER(TreeDesc), C.c_int, C.c_int, C.c_int,
                                    C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "tn_plan_stats_get": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(PlanStats)]),
@@ -96,8 +97,11 @@ def lib() -> C.CDLL:
     return _LIB
 
 
-def plan_describe(net, tree, chi: int, prec="f64", grad: bool = False) -> dict:
+def plan_describe(net, tree, chi: int, prec="f64", grad=False) -> dict:
     """The library's static schedule for (network structure, tree, chi, form) as a dict.
+
+    grad: False (forward), True (with the reverse pass) or k >= 2 (reverse pass
+    checkpointed in k segments).
 
     Needs no context and no GPU (host planning only); see tn_plan_describe in
     include/tn.h for the fields.
@@ -116,12 +120,12 @@ def plan_describe(net, tree, chi: int, prec="f64", grad: bool = False) -> dict:
     tdesc = TreeDesc(int(tree.n_inputs), int(ops.shape[0]), ops.ctypes.data_as(C.POINTER(C.c_int32)) if ops.size else None)
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     need = C.c_size_t()
-    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, 1 if grad else 0, None, 0, C.byref(need))
+    g = int(grad) if not isinstance(grad, bool) else (1 if grad else 0)
+    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, g, None, 0, C.byref(need))
     if rc != 0:
         raise TNError(rc, "tn_plan_describe failed")
     buf = C.create_string_buffer(need.value)
-    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, 1 if grad else 0, buf, need.value,
-                            C.byref(need))
+    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, g, buf, need.value, C.byref(need))
     if rc != 0:
         raise TNError(rc, "tn_plan_describe failed")
     return json.loads(buf.value.decode())
@@ -238,6 +242,10 @@ class Context:
                                                logz.ctypes.data_as(C.POINTER(C.c_double)),
                                                sign.ctypes.data_as(C.POINTER(C.c_int))))
         return logz, sign
+
+    def set_grad_segments(self, segments: int) -> None:
+        """Checkpoint tn_grad's tape in `segments` segments (1: one tape; 0: by free memory)."""
+        self._check(self._L.tn_set_grad_segments(self._h, int(segments)))
 
     def shapes(self, inst_id: int) -> List[Tuple[int, ...]]:
         """Tensor shapes of an instance's network (networks loaded from arrays)."""

@@ -203,3 +203,21 @@ def test_grad_of_zero_partition_function_is_an_error(ctx):
     with pytest.raises(TNError) as ei:
         gpu_grad(ctx, net, tr.greedy(net.bonds, net.bond_dims, chi=8), 8)
     assert ei.value.code == -7
+
+
+def test_grad_checkpointed_equals_one_tape(ctx):
+    """Checkpointed reverse pass (3 segments): the recomputation repeats the same kernels on
+    the same data, so the gradient equals the one-tape pass."""
+    n, e = nw.square_lattice(6, 6)
+    net = nw.random_network(n, e, 3, seed=3)
+    tree = tr.boundary_rows(6, 6)
+    iid = ctx.load_tree(ctx.load_network(net), tree)
+    ctx.set_grad_segments(1)
+    lz1, _, g1 = ctx.grad([iid], 5)
+    ctx.set_grad_segments(3)
+    lz3, _, g3 = ctx.grad([iid], 5)
+    ctx.set_grad_segments(0)
+    assert lz1[0] == lz3[0]
+    assert max_rel(g3[0], g1[0]) <= 1e-13
+    want = grad.contract_with_grad(net, tree, 5)
+    assert max_rel(g3[0], want.grads) <= GRAD_TOL

@@ -193,3 +193,34 @@ def test_schedule_replay_at_the_benchmark_compression_shapes():
     em = replay(net, tree, 64)
     assert em.sign[0] == want.sign
     assert abs(em.logabs[0] - want.logabs) <= TOL * abs(want.logabs), (em.logabs[0], want.logabs)
+
+
+# ---------------------------------------------------------------------------
+# checkpointed reverse pass: same gradient as one tape, less memory
+
+
+@pytest.mark.parametrize("segments", [2, 3, 7, 1000])
+def test_checkpointed_reverse_schedule_equals_one_tape(segments):
+    n, e = nw.square_lattice(6, 6)
+    net = nw.random_network(n, e, 3, seed=3)
+    tree = tr.boundary_rows(6, 6)
+    shapes = [np.shape(d) for d in net.data]
+    full = Emulator(describe(net, tree, 5, g=True), [net]).run()
+    plan = describe(net, tree, 5, g=segments)
+    assert plan["segments"] == min(segments, len(tree.ops))
+    ck = Emulator(plan, [net]).run()
+    assert ck.logabs[0] == full.logabs[0]
+    for a, b in zip(ck.grads(0, shapes), full.grads(0, shapes)):
+        assert np.array_equal(a, b)      # the recomputation repeats the same steps on the same data
+    want = grad.contract_with_grad(net, tree, 5)
+    assert max_rel(ck.grads(0, shapes), want.grads) <= GRAD_TOL
+
+
+def test_checkpointing_cuts_the_tape():
+    n, e = nw.square_lattice(16, 16)
+    net = nw.random_network(n, e, 4, seed=0)
+    tree = tr.boundary_rows(16, 16)
+    one = describe(net, tree, 64, g=True)["arena_units"]
+    many = describe(net, tree, 64, g=16)["arena_units"]
+    fwd = describe(net, tree, 64)["arena_units"]
+    assert many < 0.25 * one and many > fwd
