@@ -15,6 +15,8 @@ Modules:
   exact   -- independent references: brute-force sums over spin / edge
              configurations, row transfer matrices, closed forms, perfect
              matching counts, and full einsum contraction of tiny networks.
+  gauge   -- compression in the tree gauge of distance r (Algorithm 2's
+             spanning tree, QR inwards on virtual copies, projector form).
   grad    -- d log|Z| / d T_v: the same schedule re-run with its operands
              kept, then walked backwards (matrix-product adjoints, the exact
              power-of-two rescale, and the adjoint of the truncated SVD of
