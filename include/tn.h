@@ -193,6 +193,22 @@ int tn_contract_approx(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, in
 int tn_grad(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, int prec, double* logabsz_out,
             int* sign_out, double* const* grad_out, int on_device);
 
+/* Compressions in the tree gauge of distance r (Sec. "Bond compression
+ * strategies", tree gauge; SI: r-local spanning tree, Algorithm 2; explicit
+ * projector form).  r >= 0: before each compression of the bond between A
+ * and B, the environment within graph distance r -- a spanning tree grown
+ * from {A, B} over tensors made by contractions, closest first, then by the
+ * largest product of shared bond sizes, then by the smallest ids -- is put in
+ * the tree gauge on virtual copies (QR of each outer tensor over its bonds to
+ * its parent, R absorbed into the parent); R_A and L_B of the gauged A and B
+ * give the core SVD R_A L_B = U s V^T, and the projectors P_L = L_B V_k s^-1/2,
+ * P_R = s^-1/2 U_k^T R_A are applied to the original tensors (A <- A P_L,
+ * B <- P_R B; s^-1/2 = 0 for s <= 1e-13 s_1).  No other tensor changes.
+ * r = 0 is the projector form of the plain compression.  r = -1 (default):
+ * the plain Q-form.  Applies to later tn_contract_approx calls (tn_grad
+ * refuses it with TN_EINVAL).  Errors: TN_EINVAL for r < -1. */
+int tn_set_tree_gauge(tn_ctx* ctx, int r);
+
 /* Checkpointing of tn_grad's tape.  segments = k >= 2: the forward pass
  * copies the live tensors at the start of each of k segments of the tree's
  * ops (equal op counts) and keeps nothing else; the reverse pass then, for
@@ -208,7 +224,8 @@ int tn_set_grad_segments(tn_ctx* ctx, int segments);
 
 /* Diagnostic, needs no context and no GPU: the static schedule that
  * tn_contract_approx (grad = 0) or tn_grad (grad = 1; grad = k >= 2: with k
- * checkpointed segments) would run for this
+ * checkpointed segments) would run for this, with compressions in the
+ * tree gauge of distance gauge_r (-1: the plain form; see tn_set_tree_gauge), for this
  * network structure (the data pointers are not read), tree, chi and form
  * (schedule expansion, Algorithm 1 with explicit ops), written as one JSON
  * object: {"arena_units", "n_slots", "in_total", "grad", "segments", "in_off": [...],
@@ -221,8 +238,8 @@ int tn_set_grad_segments(tn_ctx* ctx, int segments);
  * buffers at offset * batch + instance * stride).  *need receives the size
  * including the terminating NUL; buf == NULL queries it.  Errors: TN_EINVAL
  * (bad arguments, cap too small), TN_ESHAPE / TN_EFORMAT (bad network or tree). */
-int tn_plan_describe(const tn_network_desc* net, const tn_tree_desc* tree, int chi, int prec, int grad, char* buf,
-                     size_t cap, size_t* need);
+int tn_plan_describe(const tn_network_desc* net, const tn_tree_desc* tree, int chi, int prec, int grad, int gauge_r,
+                     char* buf, size_t cap, size_t* need);
 
 /* Schedule statistics of one instance at chi (no GPU work). */
 int tn_plan_stats_get(tn_ctx* ctx, int inst_id, int chi, int prec, tn_plan_stats* out);

@@ -26,8 +26,8 @@ Readings where the paper is silent:
     spanning tree besides A and B (the SI excludes input tensors);
     `include_inputs=True` lifts that restriction (used by a pin).
   * Algorithm 2's score: the closest candidate first, then the largest
-    connectivity (log2 of the product of the sizes of the bonds u and v
-    share), then the smallest id of v, then of u.
+    connectivity (the product of the sizes of the bonds u and v share),
+    then the smallest id of v, then of u.
   * A factor whose matrix has no more rows than columns is not reduced
     (R = the matrix itself): a QR would only rotate the new bond, which the
     projectors do not see.
@@ -64,7 +64,11 @@ def spanning_tree(bonds: Dict[int, List[int]], dims: Dict[int, int], start: Sequ
 
     def conn(u, v):
         sv = set(bonds[v])
-        return sum(math.log2(dims[b]) for b in bonds[u] if b in sv)
+        p = 1
+        for b in bonds[u]:
+            if b in sv:
+                p *= dims[b]
+        return p
 
     region = set(start)
     cands: Dict[Tuple[int, int], int] = {}
@@ -97,7 +101,7 @@ def compress_gauged(T: Dict[int, np.ndarray], B: Dict[int, List[int]], dims: Dic
                     chi: int, r: int, new_bond: int, allowed):
     """Compress the bonds shared by i and j in the tree gauge of distance r.
 
-    Returns None when D_AB <= chi, else (A_new, bonds_i, B_new, bonds_j, k, gap).
+    Returns None when D_AB <= chi, else (A_new, bonds_i, B_new, bonds_j, k, gap, s_k / s_1).
     """
     ti, bi, tj, bj = T[i], B[i], T[j], B[j]
     sj, si = set(bj), set(bi)
@@ -138,6 +142,7 @@ def compress_gauged(T: Dict[int, np.ndarray], B: Dict[int, List[int]], dims: Dic
         gap = float((s[k - 1] - s[k]) / s[0])
     else:
         gap = 1.0
+    kept = float(s[k - 1] / s[0]) if len(s) and s[0] > 0 else 0.0
 
     def place(bonds, rem, mat, rem_first, shape_src, bonds_src):
         out, placed = [], False
@@ -155,7 +160,7 @@ def compress_gauged(T: Dict[int, np.ndarray], B: Dict[int, List[int]], dims: Dic
 
     ai, nbi = place(bi, ri, a_new, True, ti.shape, bi)
     bj2, nbj = place(bj, rj, b_new, False, tj.shape, bj)
-    return ai, nbi, bj2, nbj, k, gap
+    return ai, nbi, bj2, nbj, k, gap, kept
 
 
 def _matricize_d(t: np.ndarray, bonds: List[int], rows: List[int], cols: List[int], dims) -> np.ndarray:
@@ -164,7 +169,11 @@ def _matricize_d(t: np.ndarray, bonds: List[int], rows: List[int], cols: List[in
 
 
 def contract_gauged(net: Network, tree: Tree, chi: int, r: int, include_inputs: bool = False) -> Result:
-    """Algorithm 1 over the explicit ops, every compression in the tree gauge of distance r."""
+    """Algorithm 1 over the explicit ops, every compression in the tree gauge of distance r.
+
+    The result also carries min_kept: the smallest kept s_k / s_1 (the projector
+    form divides by s_k^1/2, so rounding grows as it approaches zero).
+    """
     if tree.n_inputs != net.n_tensors:
         raise ValueError("tree and network disagree on the number of tensors")
     T: Dict[int, np.ndarray] = {i: np.asarray(d, dtype=np.float64) for i, d in enumerate(net.data)}
@@ -187,7 +196,8 @@ def contract_gauged(net: Network, tree: Tree, chi: int, r: int, include_inputs: 
             out = compress_gauged(T, Bn, dims, i, j, chi, r, nxt_bond, allowed)
             if out is None:
                 continue
-            ai, nbi, bj2, nbj, k, gap = out
+            ai, nbi, bj2, nbj, k, gap, kept = out
+            res.min_kept = min(getattr(res, "min_kept", 1.0), kept)
             dims[nxt_bond] = k
             nxt_bond += 1
             ai, e1 = _rescale(ai)

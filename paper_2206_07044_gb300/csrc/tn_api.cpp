@@ -46,8 +46,9 @@ struct PlanKey {
   uint64_t hash;
   int chi, prec;
   int grad;  // 0: forward only; k >= 1: with the reverse pass, checkpointed in k segments
+  int gauge; // tree-gauge distance of the compressions (-1: plain Q-form)
   bool operator<(const PlanKey& o) const {
-    return std::tie(hash, chi, prec, grad) < std::tie(o.hash, o.chi, o.prec, o.grad);
+    return std::tie(hash, chi, prec, grad, gauge) < std::tie(o.hash, o.chi, o.prec, o.grad, o.gauge);
   }
 };
 
@@ -110,6 +111,7 @@ struct tn_ctx {
   // configuration), is captured on the second and replayed from then on
   int graph_mode = 1;
   int grad_segments = 0;  // tn_grad: 0 = choose from free device memory, k >= 1 = k segments
+  int gauge_r = -1;       // compressions in the tree gauge of this distance (-1: plain Q-form)
   uint64_t plan_serial = 0;
   uint64_t buf_gen = 0;  // bumped whenever a buffer a captured graph points into moves
   cudaStream_t cap = nullptr;
@@ -304,14 +306,14 @@ int ensure_scratch(tn_ctx* c, int batch) {
 
 // grad: 0 forward only, k >= 1 with the reverse pass in k checkpointed segments
 const tnp::Plan* get_plan(tn_ctx* c, int inst, int chi, int prec, int* rc, int grad = 0) {
-  PlanKey key{c->insts[inst].hash, chi, prec, grad};
+  PlanKey key{c->insts[inst].hash, chi, prec, grad, grad > 0 ? -1 : c->gauge_r};
   auto it = c->plans.find(key);
   if (it != c->plans.end() && same_group(c, it->second.inst_proto, inst)) return &it->second.plan;
   CachedPlan cp;
   cp.inst_proto = inst;
   const InstRec& r = c->insts[inst];
   std::string err = tnp::build_plan(c->nets[r.net].st, r.ops, r.n_inputs, chi, prec, &cp.plan, grad > 0,
-                                    grad > 0 ? grad : 1);
+                                    grad > 0 ? grad : 1, grad > 0 ? -1 : c->gauge_r);
   if (!err.empty()) {
     *rc = fail(c, TN_EFORMAT, "plan: " + err);
     return nullptr;
@@ -842,6 +844,7 @@ int tn_grad(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, doubl
             double* const* grad_out, int on_device) {
   if (!c || !inst_ids || !logabsz_out || !sign_out || !grad_out || n_inst < 1)
     return fail(c, TN_EINVAL, "bad arguments");
+  if (c->gauge_r >= 0) return fail(c, TN_EINVAL, "tn_grad is not available with the tree gauge (tn_set_tree_gauge)");
   if (chi < 1) return fail(c, TN_EINVAL, "chi must be >= 1");
   if (prec < TN_F64 || prec > TN_TF32X3) return fail(c, TN_EINVAL, "unknown precision form");
   for (int q = 0; q < n_inst; ++q) {
@@ -909,14 +912,20 @@ int tn_grad(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, doubl
   return TN_OK;
 }
 
+int tn_set_tree_gauge(tn_ctx* c, int r) {
+  if (!c || r < -1) return fail(c, TN_EINVAL, "tree-gauge distance must be >= -1");
+  c->gauge_r = r;
+  return TN_OK;
+}
+
 int tn_set_grad_segments(tn_ctx* c, int segments) {
   if (!c || segments < 0) return fail(c, TN_EINVAL, "segments must be >= 0");
   c->grad_segments = segments;
   return TN_OK;
 }
 
-int tn_plan_describe(const tn_network_desc* d, const tn_tree_desc* t, int chi, int prec, int grad, char* buf,
-                     size_t cap, size_t* need) {
+int tn_plan_describe(const tn_network_desc* d, const tn_tree_desc* t, int chi, int prec, int grad, int gauge_r,
+                     char* buf, size_t cap, size_t* need) {
   if (!d || !t || !need) return TN_EINVAL;
   if (chi < 1 || prec < TN_F64 || prec > TN_TF32X3 || t->n_ops < 0 || (t->n_ops > 0 && !t->ops)) return TN_EINVAL;
   tnp::Structure st;
@@ -926,7 +935,7 @@ int tn_plan_describe(const tn_network_desc* d, const tn_tree_desc* t, int chi, i
   tnp::Plan plan;
   std::string err;
   try {
-    err = tnp::build_plan(st, ops, t->n_inputs, chi, prec, &plan, grad != 0, grad > 1 ? grad : 1);
+    err = tnp::build_plan(st, ops, t->n_inputs, chi, prec, &plan, grad != 0, grad > 1 ? grad : 1, gauge_r);
   } catch (...) {
     return TN_ENOMEM;
   }

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <functional>
 #include <map>
+#include <set>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -584,7 +585,330 @@ struct Builder {
     }
   }
 
+  // ---- tree gauge of distance r, projector form (gauge_r >= 0)
+  int gauge_r = -1;
+
+  // Algorithm 2 over the live tensors: ordered pairs (u, v) of the r-local
+  // spanning tree grown from {i, j}; only tensors made by a contraction join;
+  // candidates are taken closest first, then by the largest product of the
+  // bond sizes u and v share, then by the smallest v, then u.
+  std::vector<std::pair<int, int>> spanning_tree(int i, int j, int r) {
+    const int n_inputs = (int)s.bonds.size();
+    std::map<int, std::vector<int>> owner;
+    for (const auto& tv : cur)
+      for (int b : vals[tv.second].bonds) owner[b].push_back(tv.first);
+    auto nbrs = [&](int u) {
+      std::set<int> out;
+      for (int b : vals[cur.at(u)].bonds)
+        for (int o : owner[b])
+          if (o != u) out.insert(o);
+      return out;
+    };
+    auto conn = [&](int u, int v) {
+      const std::vector<int>& bv = vals[cur.at(v)].bonds;
+      double p = 1.0;
+      for (int b : vals[cur.at(u)].bonds)
+        if (std::find(bv.begin(), bv.end(), b) != bv.end()) p *= (double)dim[b];
+      return p;
+    };
+    std::set<int> region = {i, j};
+    std::map<std::pair<int, int>, int> cands;
+    for (int u : {i, j})
+      for (int v : nbrs(u))
+        if (!region.count(v) && v >= n_inputs) cands[{u, v}] = 1;
+    std::vector<std::pair<int, int>> tau;
+    while (!cands.empty()) {
+      auto best = cands.begin();
+      for (auto it = cands.begin(); it != cands.end(); ++it) {
+        const auto key = std::make_tuple(it->second, -conn(it->first.first, it->first.second), it->first.second,
+                                         it->first.first);
+        const auto bk = std::make_tuple(best->second, -conn(best->first.first, best->first.second),
+                                        best->first.second, best->first.first);
+        if (key < bk) best = it;
+      }
+      const int u = best->first.first, v = best->first.second, d = best->second;
+      cands.erase(best);
+      if (region.count(v) || d > r) continue;
+      region.insert(v);
+      tau.push_back({u, v});
+      for (int w : nbrs(v))
+        if (!region.count(w) && w >= n_inputs && !cands.count({v, w})) cands[{v, w}] = d + 1;
+    }
+    return tau;
+  }
+
+  // A matrix view of value vi with rows `rows` and columns `cols` (bond lists
+  // covering the value); permutes into a temporary when neither row-major nor
+  // column-major order fits.  Temporaries are appended to `tv`.
+  PView mat_view(int vi, const std::vector<int>& rows, const std::vector<int>& cols, std::vector<int>& tv) {
+    int lay = layout_of(vals[vi].bonds, rows, cols);
+    if (lay < 0) {
+      std::vector<int> order = rows;
+      order.insert(order.end(), cols.begin(), cols.end());
+      vi = permute_to(vi, order);
+      tv.push_back(vi);
+      lay = 0;
+    }
+    const int64_t R = prod_dims(rows, dim), Cn = prod_dims(cols, dim);
+    PView p = base_view(vals[vi]);
+    if (lay == 0) {
+      p.rs = Cn;
+      p.cs = 1;
+    } else {
+      p.rs = 1;
+      p.cs = R;
+    }
+    return p;
+  }
+
+  // Compression in the tree gauge of distance r (projector form): R factors
+  // pushed inwards along the spanning tree on virtual copies, R_A and L_B from
+  // the gauged A and B, the SVD of R_A L_B, and P_L = L_B V_k s^-1/2,
+  // P_R = s^-1/2 U_k^T R_A applied to the original A and B.
+  std::string compress_gauged(int i, int j) {
+    int ia = cur.at(i), ib = cur.at(j);
+    const int ia0 = ia, ib0 = ib;
+    Split sp = split(vals[ia], vals[ib]);
+    const int64_t dab = prod_dims(sp.sh_i, dim);
+    if (dab <= chi) return "";
+    std::vector<int> sh;
+    int la, lb;
+    std::vector<int> tmps;
+    orient(ia, ib, sp, sh, la, lb, tmps);
+    const int64_t DA = prod_dims(sp.rem_i, dim), DB = prod_dims(sp.rem_j, dim);
+    if (DA > INT32_MAX || DB > INT32_MAX || dab > INT32_MAX) return "compression too large";
+    std::vector<std::pair<int64_t, int64_t>> trel;
+    auto tmp = [&](int64_t size) {
+      int64_t off;
+      PView p = temp(size, &off);
+      trel.push_back({off, size});
+      return p;
+    };
+    std::vector<int> tvals;  // temporary values (virtual copies, permutes)
+    auto qr_r = [&](int64_t m, int64_t n, const PView& A) {
+      // R factor (n x n, row-major) of an m x n matrix view, m > n
+      PView work = tmp(m * n + n);
+      work.bs = m * n;
+      PView R = tmp(n * n);
+      R.rs = n;
+      R.cs = 1;
+      Step st;
+      st.kind = ST_QR;
+      st.m = (int)m;
+      st.n = (int)n;
+      st.A = A;
+      st.work = work;
+      st.C = R;
+      st.flops = qr_flops((double)m, (double)n);
+      st.bytes = 8.0 * (2.0 * m * n + (double)n * n);
+      plan->qr_flops += st.flops;
+      add(st);
+      return R;
+    };
+    // 1. QR inwards along the spanning tree, on virtual copies
+    std::map<int, int> virt;
+    const auto tau = gauge_r > 0 ? spanning_tree(i, j, gauge_r) : std::vector<std::pair<int, int>>();
+    virt[i] = ia0;
+    virt[j] = ib0;
+    for (const auto& uv : tau) virt[uv.second] = cur.at(uv.second);
+    for (size_t q = tau.size(); q-- > 0;) {
+      const int u = tau[q].first, v = tau[q].second;
+      const std::vector<int> bv = vals[virt[v]].bonds, bu = vals[virt[u]].bonds;
+      std::vector<int> shv, rest, rest_u;
+      for (int b : bv) (std::find(bu.begin(), bu.end(), b) != bu.end() ? shv : rest).push_back(b);
+      for (int b : bu)
+        if (std::find(shv.begin(), shv.end(), b) == shv.end()) rest_u.push_back(b);
+      const int64_t Dsh = prod_dims(shv, dim), Drest = prod_dims(rest, dim), Du = prod_dims(rest_u, dim);
+      if (Dsh > INT32_MAX || Drest > INT32_MAX || Du > INT32_MAX) return "gauge region too large";
+      PView Vm = mat_view(virt[v], rest, shv, tvals);
+      PView Rv = Vm;
+      int64_t rrows = Drest;
+      if (Drest > Dsh) {
+        Rv = qr_r(Drest, Dsh, Vm);
+        rrows = Dsh;
+      }
+      const int nb = (int)dim.size();
+      dim.push_back(rrows);
+      PView Um = mat_view(virt[u], shv, rest_u, tvals);
+      std::vector<int> nbl = {nb};
+      nbl.insert(nbl.end(), rest_u.begin(), rest_u.end());
+      const int nu = new_arena_value(nbl);
+      tvals.push_back(nu);
+      PView C = base_view(vals[nu]);
+      C.rs = Du;
+      C.cs = 1;
+      gemm((int)rrows, (int)Du, (int)Dsh, Rv, Um, C);
+      virt[u] = nu;
+    }
+    // 2. R_A (rA x dab) and L_B (dab x rB) from the gauged A and B
+    std::vector<int> restA, restB;
+    for (int b : vals[virt[i]].bonds)
+      if (std::find(sh.begin(), sh.end(), b) == sh.end()) restA.push_back(b);
+    for (int b : vals[virt[j]].bonds)
+      if (std::find(sh.begin(), sh.end(), b) == sh.end()) restB.push_back(b);
+    const int64_t DAg = prod_dims(restA, dim), DBg = prod_dims(restB, dim);
+    if (DAg > INT32_MAX || DBg > INT32_MAX) return "compression too large";
+    PView RA = mat_view(virt[i], restA, sh, tvals);
+    int64_t rA = DAg;
+    if (DAg > dab) {
+      RA = qr_r(DAg, dab, RA);
+      rA = dab;
+    }
+    PView LB = mat_view(virt[j], sh, restB, tvals);
+    int64_t rB = DBg;
+    if (DBg > dab) {
+      PView Bt = LB;
+      std::swap(Bt.rs, Bt.cs);
+      LB = qr_r(DBg, dab, Bt);
+      std::swap(LB.rs, LB.cs);
+      rB = dab;
+    }
+    const int64_t kk = std::min<int64_t>(chi, std::min(rA, rB));
+    // 3. SVD of the core R_A L_B (two precisions, V kept), sorted factors
+    const bool tall = rA >= rB;
+    const int64_t Jm = tall ? rA : rB, Jn = tall ? rB : rA;
+    PView M0 = tmp(rA * rB);
+    if (tall) { M0.rs = 1; M0.cs = rA; } else { M0.rs = rB; M0.cs = 1; }
+    gemm((int)rA, (int)rB, (int)dab, RA, LB, M0);
+    PView M0c = M0;
+    M0c.rs = 1;
+    M0c.cs = Jm;
+    PView G32 = tmp((Jm * Jn + 1) / 2), V32 = tmp((Jn * Jn + 1) / 2);
+    {
+      Step st;
+      st.kind = ST_TO_F32;
+      st.src = M0;
+      st.dst = G32;
+      st.count = Jm * Jn;
+      st.fbs_dst = 2 * G32.bs;
+      add(st);
+      Step jst;
+      jst.kind = ST_JACOBI32;
+      jst.m = (int)Jm;
+      jst.n = (int)Jn;
+      jst.C = G32;
+      jst.aux1 = V32;
+      jst.fbs_src = 2 * G32.bs;
+      jst.fbs_dst = 2 * V32.bs;
+      add(jst);
+    }
+    PView Vd = tmp(Jn * Jn), V = tmp(Jn * Jn), E = tmp(Jn * Jn);
+    {
+      Step st;
+      st.kind = ST_TO_F64;
+      st.src = V32;
+      st.dst = Vd;
+      st.out1 = V;
+      st.count = Jn * Jn;
+      st.fbs_src = 2 * V32.bs;
+      add(st);
+    }
+    PView VdT = Vd, VdN = Vd, Ec = E, Vc = V;
+    VdT.rs = Jn; VdT.cs = 1;
+    VdN.rs = 1; VdN.cs = Jn;
+    Ec.rs = Jn; Ec.cs = 1;
+    Vc.rs = 1; Vc.cs = Jn;
+    gemm((int)Jn, (int)Jn, (int)Jn, VdT, VdN, Ec, 1.0, 0.0, true);
+    gemm((int)Jn, (int)Jn, (int)Jn, VdN, Ec, Vc, -0.5, 1.5, true);
+    {
+      Step cp;
+      cp.kind = ST_COPY;
+      cp.src = V;
+      cp.dst = Vd;
+      cp.count = Jn * Jn;
+      add(cp);
+    }
+    PView VT = V;
+    VT.rs = Jn;
+    VT.cs = 1;
+    gemm((int)Jn, (int)Jn, (int)Jn, VT, Vc, Ec, 1.0, 0.0, true);
+    gemm((int)Jn, (int)Jn, (int)Jn, VdN, Ec, Vc, -0.5, 1.5, true);
+    PView G = tmp(Jm * Jn);
+    G.rs = 1;
+    G.cs = Jm;
+    gemm((int)Jm, (int)Jn, (int)Jn, M0c, Vc, G, 1.0, 0.0, true);
+    PView sig = tmp(Jn);
+    {
+      Step st;
+      st.kind = ST_JACOBI;
+      st.m = (int)Jm;
+      st.n = (int)Jn;
+      st.C = G;
+      st.aux1 = V;
+      st.aux2 = sig;
+      st.init_v = 0;
+      st.no_v = 0;
+      st.jac_tol = 1e-8;
+      st.flops = svd_flops((double)rA, (double)rB);
+      plan->svd_flops += st.flops;
+      add(st);
+    }
+    const int64_t q = Jn;
+    PView U = tmp(rA * q), W = tmp(rB * q), sv = tmp(q), Us = tmp(rA * kk), Ws = tmp(rB * kk);
+    {
+      Step st;
+      st.kind = ST_SVD_FACTORS;
+      st.m = (int)Jm;
+      st.n = (int)Jn;
+      st.k = (int)kk;
+      st.flag = tall ? 1 : 0;
+      st.C = G;
+      st.aux1 = V;
+      st.aux2 = sig;
+      st.out1 = U;
+      st.out2 = W;
+      st.work = sv;
+      st.A = Us;
+      st.B = Ws;
+      add(st);
+    }
+    Us.rs = 1; Us.cs = rA;
+    Ws.rs = 1; Ws.cs = rB;
+    // 4. projectors P_L = L_B W_s (dab x k) and P_R^T = R_A^T U_s (dab x k)
+    PView PL = tmp(dab * kk), PRt = tmp(dab * kk);
+    PL.rs = kk; PL.cs = 1;
+    PRt.rs = kk; PRt.cs = 1;
+    gemm((int)dab, (int)kk, (int)rB, LB, Ws, PL);
+    PView RAt = RA;
+    std::swap(RAt.rs, RAt.cs);
+    gemm((int)dab, (int)kk, (int)rA, RAt, Us, PRt);
+    // 5. A <- A P_L, B^T <- B^T P_R^T into the new tensors (column-major, bonds [new, rest...])
+    const int nbond = (int)dim.size();
+    dim.push_back(kk);
+    std::vector<int> bi = {nbond};
+    bi.insert(bi.end(), sp.rem_i.begin(), sp.rem_i.end());
+    std::vector<int> bj = {nbond};
+    bj.insert(bj.end(), sp.rem_j.begin(), sp.rem_j.end());
+    const int na = new_arena_value(bi), nbv = new_arena_value(bj);
+    PView A = base_view(vals[ia]);
+    if (la == 0) { A.rs = dab; A.cs = 1; } else { A.rs = 1; A.cs = DA; }
+    PView B = base_view(vals[ib]);
+    if (lb == 0) { B.rs = DB; B.cs = 1; } else { B.rs = 1; B.cs = dab; }
+    PView Ab = base_view(vals[na]), Bb = base_view(vals[nbv]);
+    Ab.rs = 1; Ab.cs = DA;
+    Bb.rs = 1; Bb.cs = DB;
+    gemm((int)DA, (int)kk, (int)dab, A, PL, Ab);
+    PView Bt = B;
+    std::swap(Bt.rs, Bt.cs);
+    gemm((int)DB, (int)kk, (int)dab, Bt, PRt, Bb);
+    plan->gemm_flops += 2.0 * DA * dab * (double)kk + 2.0 * DB * dab * (double)kk;
+    rescale(na);
+    rescale(nbv);
+    for (auto& t : trel) rel(t.first, t.second);
+    for (int t : tvals) release_value(t);
+    for (int t : tmps) release_value(t);
+    release_value(ia0);
+    release_value(ib0);
+    cur[i] = na;
+    cur[j] = nbv;
+    record(i, na);
+    record(j, nbv);
+    plan->n_compressions++;
+    return "";
+  }
+
   std::string compress(int i, int j) {
+    if (gauge_r >= 0) return compress_gauged(i, j);
     int ia = cur.at(i), ib = cur.at(j);
     const int ia0 = ia, ib0 = ib;
     Split sp = split(vals[ia], vals[ib]);
@@ -977,11 +1301,12 @@ std::string build_checkpointed(Builder& bld, const std::vector<int32_t>& ops, in
 }  // namespace
 
 std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int n_inputs, int chi,
-                       int prec, Plan* out, bool grad, int segments) {
+                       int prec, Plan* out, bool grad, int segments, int gauge_r) {
   std::string err = validate_tree(s, ops, n_inputs);
   if (!err.empty()) return err;
   if (chi < 1) return "chi must be >= 1";
   if (segments < 1) return "segments must be >= 1";
+  if (grad && gauge_r >= 0) return "the reverse pass is not available with the tree gauge";
   *out = Plan();
   out->chi = chi;
   out->prec = prec;
@@ -990,6 +1315,8 @@ std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int 
   bld.grad = grad;
   bld.keep = grad;
   bld.keep_v = grad;
+  bld.gauge_r = gauge_r;
+  out->gauge_r = gauge_r;
   out->grad = grad;
   out->in_total = s.in_total;
   const int nt = (int)s.bonds.size();

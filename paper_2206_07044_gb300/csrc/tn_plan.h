@@ -103,6 +103,7 @@ struct Plan {
   bool grad = false;
   int n_slots = 0;           // rescale tape slots (ints per instance)
   int segments = 1;          // checkpointed segments of the reverse pass (1: one tape of the whole pass)
+  int gauge_r = -1;          // tree-gauge distance of the compressions (-1: plain Q-form)
   int64_t in_total = 0;      // elements of the input block per instance
   double bwd_flops = 0;      // GEMM flops of the reverse pass
   uint64_t serial = 0;       // set by the owner; distinct per plan built (keys captured graphs)
@@ -120,8 +121,10 @@ struct Structure {
 // grad: also emit the reverse pass (d log|Z| / d inputs); segments > 1 (with
 // grad): checkpoint the live tensors at that many segment starts and
 // recompute each segment's operands just before its reverse steps.
+// gauge_r >= 0: compressions in the tree gauge of distance gauge_r, projector
+// form (forward only); -1: the plain Q-form.
 std::string build_plan(const Structure& s, const std::vector<int32_t>& ops, int n_inputs, int chi,
-                       int prec, Plan* out, bool grad = false, int segments = 1);
+                       int prec, Plan* out, bool grad = false, int segments = 1, int gauge_r = -1);
 
 // Validate a tree against a structure without chi (ids, order, final scalar).
 std::string validate_tree(const Structure& s, const std::vector<int32_t>& ops, int n_inputs);

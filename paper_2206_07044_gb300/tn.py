@@ -64,8 +64,9 @@ SIGNATURES = {
     "tn_grad": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_double),
                           C.POINTER(C.c_int), C.POINTER(C.c_void_p), C.c_int]),
     "tn_set_grad_segments": (C.c_int, [C.c_void_p, C.c_int]),
-    "tn_plan_describe": (C.c_int, [C.POINTER(NetworkDesc), C.POINTER(TreeDesc), C.c_int, C.c_int, C.c_int,
+    "tn_plan_describe": (C.c_int, [C.POINTER(NetworkDesc), C.POINTER(TreeDesc), C.c_int, C.c_int, C.c_int, C.c_int,
                                    C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "tn_set_tree_gauge": (C.c_int, [C.c_void_p, C.c_int]),
     "tn_plan_stats_get": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(PlanStats)]),
     "tn_debug_tensor": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_int, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int32),
@@ -97,7 +98,7 @@ def lib() -> C.CDLL:
     return _LIB
 
 
-def plan_describe(net, tree, chi: int, prec="f64", grad=False) -> dict:
+def plan_describe(net, tree, chi: int, prec="f64", grad=False, gauge_r: int = -1) -> dict:
     """The library's static schedule for (network structure, tree, chi, form) as a dict.
 
     grad: False (forward), True (with the reverse pass) or k >= 2 (reverse pass
@@ -121,11 +122,12 @@ def plan_describe(net, tree, chi: int, prec="f64", grad=False) -> dict:
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     need = C.c_size_t()
     g = int(grad) if not isinstance(grad, bool) else (1 if grad else 0)
-    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, g, None, 0, C.byref(need))
+    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, g, int(gauge_r), None, 0, C.byref(need))
     if rc != 0:
         raise TNError(rc, "tn_plan_describe failed")
     buf = C.create_string_buffer(need.value)
-    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, g, buf, need.value, C.byref(need))
+    rc = L.tn_plan_describe(C.byref(desc), C.byref(tdesc), int(chi), p, g, int(gauge_r), buf, need.value,
+                            C.byref(need))
     if rc != 0:
         raise TNError(rc, "tn_plan_describe failed")
     return json.loads(buf.value.decode())
@@ -242,6 +244,10 @@ class Context:
                                                logz.ctypes.data_as(C.POINTER(C.c_double)),
                                                sign.ctypes.data_as(C.POINTER(C.c_int))))
         return logz, sign
+
+    def set_tree_gauge(self, r: int) -> None:
+        """Compress in the tree gauge of distance r (projector form); -1 restores the plain Q-form."""
+        self._check(self._L.tn_set_tree_gauge(self._h, int(r)))
 
     def set_grad_segments(self, segments: int) -> None:
         """Checkpoint tn_grad's tape in `segments` segments (1: one tape; 0: by free memory)."""

@@ -430,3 +430,46 @@ def test_mixed_form_random_normal_within_format_roundoff(ctx):
     for prec, tol in (("tf32x3", 2.0 ** -11), ("tf32", 2.0 ** -8)):
         got, sign = gpu_run(ctx, net, tree, 9, prec)
         assert abs(got - want.logabs) <= tol * abs(want.logabs), (prec, got, want.logabs)
+
+
+# ---------------------------------------------------------------------------
+# tree gauge of distance r (projector form) against oracle.gauge
+
+
+@pytest.mark.parametrize("r", [1, 2, 4])
+def test_tree_gauge_ising_8x8_chi4(ctx, r):
+    from oracle import gauge
+    from paper_2206_07044_gb300 import Context
+    n, edges = nw.square_lattice(8, 8)
+    net = nw.ising_network(n, edges, 0.44)
+    tree = tr.boundary_rows(8, 8)
+    want = gauge.contract_gauged(net, tree, 4, r)
+    assert min(d[2] for d in want.diag) > 1e-8 and want.min_kept > 1e-6
+    ctx.set_tree_gauge(r)
+    try:
+        got, sign = gpu_run(ctx, net, tree, 4)
+    finally:
+        ctx.set_tree_gauge(-1)
+    assert sign == want.sign
+    assert abs(got - want.logabs) <= TOL * abs(want.logabs), (r, got, want.logabs)
+    # the gauge pays off: closer to the transfer matrix than the plain compression
+    tm = exact.ising_transfer_2d(8, 8, 0.44)["lnZ"]
+    plain = approx.contract(net, tree, 4).logabs
+    assert abs(got - tm) < 0.1 * abs(plain - tm)
+
+
+def test_tree_gauge_random_uniform_batch(ctx):
+    from oracle import gauge
+    n, edges = nw.square_lattice(6, 7)
+    tree = tr.boundary_rows(6, 7)
+    nets = [nw.random_network(n, edges, 3, seed=4 + s, dist="uniform", lam=0.0) for s in range(3)]
+    ids = [ctx.load_tree(ctx.load_network(x), tree) for x in nets]
+    ctx.set_tree_gauge(2)
+    try:
+        lz, sg = ctx.contract(ids, 3)
+    finally:
+        ctx.set_tree_gauge(-1)
+    for x, l, s in zip(nets, lz, sg):
+        want = gauge.contract_gauged(x, tree, 3, 2)
+        assert want.min_kept > 1e-6 and min(d[2] for d in want.diag) > 1e-8
+        assert s == want.sign and abs(l - want.logabs) <= TOL * abs(want.logabs)

@@ -224,3 +224,35 @@ def test_checkpointing_cuts_the_tape():
     many = describe(net, tree, 64, g=16)["arena_units"]
     fwd = describe(net, tree, 64)["arena_units"]
     assert many < 0.25 * one and many > fwd
+
+
+# ---------------------------------------------------------------------------
+# tree gauge (projector form): the planned schedule against oracle.gauge
+
+
+def gauge_cases():
+    out = []
+    n, e = nw.square_lattice(8, 8)
+    out.append(("ising 8x8 chi4", nw.ising_network(n, e, 0.44), tr.boundary_rows(8, 8), 4))
+    n, e = nw.square_lattice(6, 7)
+    out.append(("urand 6x7 chi3", nw.random_network(n, e, 3, seed=4, dist="uniform", lam=0.0),
+                tr.boundary_rows(6, 7), 3))
+    net = nw.random_network(n, e, 3, seed=7)
+    out.append(("normal 6x7 greedy chi5", net, tr.greedy(net.bonds, net.bond_dims, chi=5, seed=0), 5))
+    return out
+
+
+GAUGE = gauge_cases()
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 4])
+@pytest.mark.parametrize("name,net,tree,chi", GAUGE, ids=[c[0] for c in GAUGE])
+def test_tree_gauge_schedule_replay_matches_oracle(name, net, tree, chi, r):
+    from oracle import gauge
+    want = gauge.contract_gauged(net, tree, chi, r)
+    assert want.compressions > 0 and min(d[2] for d in want.diag) > 1e-8
+    assert getattr(want, "min_kept", 1.0) > 1e-6, "kept values near zero: the projector form is ill-conditioned"
+    from paper_2206_07044_gb300 import tn
+    em = Emulator(tn.plan_describe(net, tree, chi, "f64", False, r), [net]).run()
+    assert em.sign[0] == want.sign
+    assert abs(em.logabs[0] - want.logabs) <= TOL * abs(want.logabs), (name, r, em.logabs[0], want.logabs)
