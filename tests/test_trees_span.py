@@ -75,3 +75,39 @@ def test_hyper_search_beats_the_boundary_order_on_16x16():
     assert cost == tr.trace_cost(net.bonds, net.bond_dims, tree, 64)["total"]
     boundary = tr.trace_cost(net.bonds, net.bond_dims, tr.boundary_rows(16, 16), 64)["total"]
     assert cost < boundary, (cost, boundary, params)
+
+
+# ---------------------------------------------------------------------------
+# layer-by-layer boundary order for cubic lattices
+
+
+def test_boundary_layers_contract_exactly_and_replay():
+    n, e = nw.cubic_lattice(3, 2, 3)
+    net = nw.random_network(n, e, 2, seed=1)
+    t = tr.boundary_layers(3, 2, 3)
+    z = exact.einsum_contract(net)
+    r = approx.contract_exact(net, t)
+    assert r.sign == np.sign(z) and abs(r.logabs - np.log(abs(z))) < 1e-12 * max(1.0, abs(r.logabs))
+    from paper_2206_07044_gb300 import build, tn
+    build.build()
+    n, e = nw.cubic_lattice(3, 3, 3)
+    net = nw.ising_network(n, e, 0.5, nw.spin_glass_couplings(len(e), seed=2))
+    t = tr.boundary_layers(3, 3, 3)
+    want = approx.contract(net, t, 4)
+    assert want.compressions > 0 and min(d[2] for d in want.diag) > 1e-8
+    em = Emulator(tn.plan_describe(net, t, 4), [net]).run()
+    assert em.sign[0] == want.sign and abs(em.logabs[0] - want.logabs) <= 1e-10 * abs(want.logabs)
+
+
+def test_boundary_layers_make_the_8x8x8_glass_plannable_at_chi_32():
+    """8x8x8 +-J glass at chi = 32: a few GB per instance on the layered order
+    (the best of 24 sampled Span trees needs about 280 GB)."""
+    from paper_2206_07044_gb300 import build, tn
+    build.build()
+    n, e = nw.cubic_lattice(8, 8, 8)
+    net = nw.ising_network(n, e, 0.5, nw.spin_glass_couplings(len(e), seed=0))
+    t = tr.boundary_layers(8, 8, 8)
+    cost = tr.trace_cost(net.bonds, net.bond_dims, t, 32)
+    assert cost["total"] < 1e13 and cost["peak"] < 1e9
+    p = tn.plan_describe(net, t, 32)
+    assert p["arena_units"] * 8 < 4e9

@@ -59,6 +59,48 @@ def boundary_rows(lx: int, ly: int) -> Tree:
     return Tree(n, ops)
 
 
+def boundary_layers(lx: int, ly: int, lz: int) -> Tree:
+    """Layer-by-layer boundary order for ``networks.cubic_lattice(lx, ly, lz)`` ids
+    (the 3D counterpart of boundary_rows: a boundary PEPS swept along z).
+
+    Layer 0 is the initial boundary.  For each next layer, site (x, y, z) is
+    contracted into boundary tensor (x, y) in row-major order, and right after
+    each absorption the bonds to the already-updated neighbours (x-1, y) and
+    (x, y-1) are compressed.  Finally the boundary PEPS itself is contracted
+    by boundary_rows' order (row y absorbed into the row MPS, then its bonds
+    compressed left to right) and the last MPS left to right.
+    """
+    n = lx * ly * lz
+    nxt = n
+    ops: List[tuple] = []
+    b = list(range(lx * ly))
+    for z in range(1, lz):
+        for y in range(ly):
+            for x in range(lx):
+                q = y * lx + x
+                ops.append(("C", b[q], (z * ly + y) * lx + x, nxt))
+                b[q] = nxt
+                nxt += 1
+                if x > 0:
+                    ops.append(("S", b[q - 1], b[q]))
+                if y > 0:
+                    ops.append(("S", b[q - lx], b[q]))
+    m = [b[x] for x in range(lx)]
+    for y in range(1, ly):
+        for x in range(lx):
+            ops.append(("C", m[x], b[y * lx + x], nxt))
+            m[x] = nxt
+            nxt += 1
+        for x in range(lx - 1):
+            ops.append(("S", m[x], m[x + 1]))
+    acc = m[0]
+    for x in range(1, lx):
+        ops.append(("C", acc, m[x], nxt))
+        acc = nxt
+        nxt += 1
+    return Tree(n, ops)
+
+
 def _neighbours(bonds: Dict[int, List[int]], bond_owner: Dict[int, List[int]], t: int) -> List[int]:
     out = set()
     for b in bonds[t]:
