@@ -256,3 +256,16 @@ def test_tree_gauge_schedule_replay_matches_oracle(name, net, tree, chi, r):
     em = Emulator(tn.plan_describe(net, tree, chi, "f64", False, r), [net]).run()
     assert em.sign[0] == want.sign
     assert abs(em.logabs[0] - want.logabs) <= TOL * abs(want.logabs), (name, r, em.logabs[0], want.logabs)
+
+
+def test_beta_sweep_configuration_plans_within_one_gpu():
+    """64x64 Ising, chi = 128, TF32 form: the 256-instance beta sweep fits in HBM
+    (about 0.07 GB of arena per instance; with the gradient in 64 segments about 3 GB)."""
+    n, e = nw.square_lattice(64, 64)
+    net = nw.ising_network(n, e, 0.44)
+    tree = tr.boundary_rows(64, 64)
+    p = describe(net, tree, 128, "tf32")
+    assert p["arena_units"] * 8 * 256 < 64e9
+    assert max(st["n"] for st in p["steps"] if st["kind"] == 3) == 256
+    pg = describe(net, tree, 128, "tf32", g=64)
+    assert pg["arena_units"] * 8 < 8e9
