@@ -196,11 +196,9 @@ cudaError_t apply_q_f64(int m, int n, const double* work, int64_t work_bs, doubl
   if (batch > 65535) return cudaErrorInvalidValue;
   const double* taus = work + (int64_t)batch * work_bs;
   size_t smem = (m <= kVSmem) ? (size_t)m * sizeof(double) : 0;
-  static bool attr_done = false;
-  if (!attr_done) {
+  once_per_device((const void*)apply_q_kernel, [] {
     cudaFuncSetAttribute(apply_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kVSmem * (int)sizeof(double));
-    attr_done = true;
-  }
+  });
   const int per_cta = kThreads / 32;
   dim3 grid((k + per_cta - 1) / per_cta, batch);
   apply_q_kernel<<<grid, kThreads, smem, s>>>(m, n, work, work_bs, taus, X, x_bs, k, trans);
@@ -212,14 +210,13 @@ namespace {
 constexpr size_t kQrSmemCap = 210 * 1024;
 
 void ensure_qr_attrs() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemCap);
-  cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kVSmem * (int)sizeof(double));
-  cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  done = true;
+  once_per_device((const void*)qr_cluster_kernel<true>, [] {
+    cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemCap);
+    cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kVSmem * (int)sizeof(double));
+    cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  });
 }
 
 template <bool kSmem>

@@ -415,12 +415,10 @@ cudaError_t launch_jacobi(const JacArgs<T>& a, int batch, cudaStream_t s) {
   int pmax = a.n / 16;
   if (pmax > 16) pmax = 16;
   if (pmax < 1) pmax = 1;
-  static bool attr_set = false;
-  if (!attr_set) {
+  once_per_device((const void*)block_jacobi_kernel<T>, [] {
     cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
-    attr_set = true;
-  }
+  });
   const bool has_v = a.V != nullptr;
   auto smem_of = [&](int q) {
     const size_t sm = block_smem<T>(a.m, a.n, q, has_v);

@@ -14,6 +14,23 @@
 
 namespace tnk {
 
+// Runs set(), which sets function attributes, once per (key, device): CUDA
+// function attributes belong to the device's context, so a process that uses
+// several GPUs must set them on each.
+template <typename F>
+inline void once_per_device(const void* key, F set) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, bool> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  bool& d = done[{key, dev}];
+  if (!d) {
+    set();
+    d = true;
+  }
+}
+
 // Clusters of `cluster` CTAs (threads, dynamic smem bytes) of kernel `func` that
 // can be resident at once on the current device (0 if none or on error).
 inline int resident_clusters(const void* func, int cluster, int threads, size_t smem) {
