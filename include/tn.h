@@ -11,8 +11,12 @@
  *             their sizes D_AB exceeds chi (Sec. "Bond compression strategies"):
  *             QR of A, LQ of B, truncated SVD of R_A R_B to
  *             k = min(chi, D_A, D_B) singular values, sqrt(sigma) absorbed on
- *             both sides (Eq. "svd"), applied in the equivalent projector form
- *             A P_L, P_R B of the SI section "Explicit projector form".
+ *             both sides (Eq. "svd"): A_bar = Q_A U_k sigma^1/2 and
+ *             B_bar = sigma^1/2 V_k^T Q_B, with the Householder products of the
+ *             two QRs applied to the zero-padded factors (the Q-form; Q is
+ *             never formed).  The equivalent projector form A P_L, P_R B of the
+ *             SI section "Explicit projector form" is used only for
+ *             compressions in the tree gauge (tn_set_tree_gauge).
  *
  * A power-of-two running log-norm keeps every intermediate in range, so log|Z|
  * never overflows.  All arithmetic runs in CUDA kernels on the GPU; there is
@@ -104,8 +108,34 @@ typedef struct {
   int64_t kernel_launches;    /* kernels per evaluation of this instance       */
 } tn_plan_stats;
 
-/* Create a context on CUDA device `device`.  *out receives the context. */
-int tn_create(tn_ctx** out, int device);
+/* Options of a context (tn_create).  Fill with tn_options_default, then
+ * change fields; struct_size lets later versions add fields at the end.
+ *   graph_mode         initial tn_set_graph_mode value (default 1)
+ *   grad_segments      initial tn_set_grad_segments value (default 0)
+ *   tape_budget_bytes  tn_grad with grad_segments 0: the device bytes the
+ *                      tape of one batch may take before the pass is
+ *                      checkpointed in ceil(sqrt(ops)) segments
+ *                      (default 0: half the free device memory)
+ *   debug_max_sweeps   > 0: cap the FP64 Jacobi sweep loop of every core
+ *                      SVD at this many sweeps (a matrix that needs more
+ *                      makes the call return TN_ENOCONV); 0: 60 sweeps.
+ *                      For tests of the bounded loop; leave 0 otherwise. */
+typedef struct {
+  int32_t struct_size;
+  int32_t graph_mode;
+  int32_t grad_segments;
+  int32_t debug_max_sweeps;
+  double tape_budget_bytes;
+} tn_options;
+
+/* Default options (struct_size = sizeof(tn_options)). */
+void tn_options_default(tn_options* opt);
+
+/* Create a context on CUDA device `device` with options `opt` (NULL: the
+ * defaults).  *out receives the context.  Errors: TN_EINVAL (NULL out, a
+ * struct_size smaller than the first version's, negative fields), TN_ECUDA
+ * (no such device). */
+int tn_create(tn_ctx** out, int device, const tn_options* opt);
 
 /* Destroy a context and free its device memory.  NULL is ignored. */
 void tn_destroy(tn_ctx* ctx);
@@ -286,8 +316,9 @@ int tn_kernel_times(tn_ctx* ctx, int cap, const char** names, int64_t* launches,
  * device current; make that first call before any stream capture.  All calls
  * on a device share the one array (what must start at zero is cleared on
  * each call), so calls that overlap on the GPU -- on two streams or from two
- * threads -- race; serialise them.  Results equal tn_contract_approx's for a
- * batch of one (same schedule, same kernels). */
+ * threads -- race; serialise them.  Results equal those of tn_contract_approx
+ * for a batch of one in the FP64 form with the plain Q-form compressions (no
+ * tree gauge): the same schedule and the same kernels. */
 int tn_contract_approx_noalloc(const tn_network_desc* net, const tn_tree_desc* tree, int chi,
                                void* cuda_stream, double* logabsz_out, int* sign_out, char* err_msg,
                                size_t err_cap);

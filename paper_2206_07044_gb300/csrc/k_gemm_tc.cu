@@ -324,9 +324,10 @@ cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int m, int n
   const int stages = kMode == 2 ? 3 : kStages;
   const int split = kMode == 2 ? 2 : 1;
   const size_t smem = 1024 + (size_t)stages * split * (kBM * 128 + BN * 128);
-  once_per_device((const void*)gemm_tc_kernel<kMode, BN>, [&] {
-    cudaFuncSetAttribute(gemm_tc_kernel<kMode, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t ae = once_per_device((const void*)gemm_tc_kernel<kMode, BN>, [&] {
+    return cudaFuncSetAttribute(gemm_tc_kernel<kMode, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
+  if (ae != cudaSuccess) return ae;
   dim3 grid(tiles_n, tiles_m, batch);
   gemm_tc_kernel<kMode, BN><<<grid, kTcThreads, smem, s>>>(ma, mb, m, n, kblocks, alpha, C, arows, brows, alo, blo,
                                                            err);

@@ -196,9 +196,11 @@ cudaError_t apply_q_f64(int m, int n, const double* work, int64_t work_bs, doubl
   if (batch > 65535) return cudaErrorInvalidValue;
   const double* taus = work + (int64_t)batch * work_bs;
   size_t smem = (m <= kVSmem) ? (size_t)m * sizeof(double) : 0;
-  once_per_device((const void*)apply_q_kernel, [] {
-    cudaFuncSetAttribute(apply_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kVSmem * (int)sizeof(double));
+  cudaError_t ae = once_per_device((const void*)apply_q_kernel, [] {
+    return cudaFuncSetAttribute(apply_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kVSmem * (int)sizeof(double));
   });
+  if (ae != cudaSuccess) return ae;
   const int per_cta = kThreads / 32;
   dim3 grid((k + per_cta - 1) / per_cta, batch);
   apply_q_kernel<<<grid, kThreads, smem, s>>>(m, n, work, work_bs, taus, X, x_bs, k, trans);
@@ -209,13 +211,18 @@ namespace {
 
 constexpr size_t kQrSmemCap = 210 * 1024;
 
-void ensure_qr_attrs() {
-  once_per_device((const void*)qr_cluster_kernel<true>, [] {
-    cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemCap);
-    cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kVSmem * (int)sizeof(double));
-    cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+cudaError_t ensure_qr_attrs() {
+  return once_per_device((const void*)qr_cluster_kernel<true>, [] {
+    cudaError_t e =
+        cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemCap);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(qr_cluster_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kVSmem * (int)sizeof(double));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(qr_cluster_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
   });
 }
 
@@ -243,7 +250,8 @@ cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW 
                      cudaStream_t s) {
   if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
   if (batch > 65535) return cudaErrorInvalidValue;
-  ensure_qr_attrs();
+  cudaError_t ae = ensure_qr_attrs();
+  if (ae != cudaSuccess) return ae;
   // tau scratch sits after the batch of working copies
   double* taus = work + (int64_t)batch * work_bs;
   // cluster size: at least ~16 columns per CTA and at most 16 CTAs (non-portable

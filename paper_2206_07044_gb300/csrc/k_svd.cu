@@ -415,10 +415,13 @@ cudaError_t launch_jacobi(const JacArgs<T>& a, int batch, cudaStream_t s) {
   int pmax = a.n / 16;
   if (pmax > 16) pmax = 16;
   if (pmax < 1) pmax = 1;
-  once_per_device((const void*)block_jacobi_kernel<T>, [] {
-    cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  cudaError_t ae = once_per_device((const void*)block_jacobi_kernel<T>, [] {
+    cudaError_t e = cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    return e;
   });
+  if (ae != cudaSuccess) return ae;
   const bool has_v = a.V != nullptr;
   auto smem_of = [&](int q) {
     const size_t sm = block_smem<T>(a.m, a.n, q, has_v);
@@ -561,12 +564,12 @@ cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64
 
 cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int64_t v_bs, double* sig,
                            int64_t sig_bs, int* ws, DevState st, int init_v, int batch, cudaStream_t s,
-                           unsigned long long* sweep_ctr, double sig_tol) {
+                           unsigned long long* sweep_ctr, double sig_tol, int max_sweeps) {
   // rotate down to sqrt(m) eps (the cut's subspace error is that over the gap);
   // convergence is judged by the looser sig_tol, so rounding-level rotations
   // never keep the sweep loop alive
   const double rt = sqrt((double)(m > 16 ? m : 16));
-  JacArgs<double> a{m, n, G, g_bs, V, v_bs, sig, sig_bs, ws, st.status, init_v, 60,
+  JacArgs<double> a{m, n, G, g_bs, V, v_bs, sig, sig_bs, ws, st.status, init_v, max_sweeps > 0 ? max_sweeps : 60,
                     rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, 0.0, 0.0, sweep_ctr};
   return launch_jacobi(a, batch, s);
 }

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/tn.h"
+#include "tn_exec.h"
 #include "tn_kernels.h"
 #include "tn_plan.h"
 
@@ -112,6 +113,8 @@ struct tn_ctx {
   int graph_mode = 1;
   int grad_segments = 0;  // tn_grad: 0 = choose from free device memory, k >= 1 = k segments
   int gauge_r = -1;       // compressions in the tree gauge of this distance (-1: plain Q-form)
+  double tape_budget = 0.0;  // tn_grad: tape bytes before checkpointing (0: half the free device memory)
+  int opt_max_sweeps = 0;    // > 0: FP64 Jacobi sweep cap (tests of the bounded loop)
   uint64_t plan_serial = 0;
   uint64_t buf_gen = 0;  // bumped whenever a buffer a captured graph points into moves
   cudaStream_t cap = nullptr;
@@ -161,43 +164,9 @@ cudaError_t ensure(T** p, size_t* have, size_t need) {
 
 int load_structure(tn_ctx* c, int32_t n_bonds, const int64_t* bond_dims, int32_t n_tensors,
                    const int32_t* ndims, const int32_t* bond_ids, tnp::Structure* st) {
-  if (n_bonds < 0 || n_tensors < 1) return fail(c, TN_EINVAL, "network needs >= 1 tensor");
-  if (n_bonds > 0 && !bond_dims) return fail(c, TN_EINVAL, "bond_dims is NULL");
-  if (!ndims || (n_bonds > 0 && !bond_ids)) return fail(c, TN_EINVAL, "ndims / bond_ids is NULL");
-  st->bond_dims.assign(bond_dims, bond_dims + n_bonds);
-  for (int64_t d : st->bond_dims)
-    if (d < 1 || d > (1ll << 31)) return fail(c, TN_ESHAPE, "bond size out of range");
-  std::vector<int> count(n_bonds, 0), first(n_bonds, -1);
-  st->bonds.assign(n_tensors, {});
-  st->in_off.assign(n_tensors, 0);
-  int64_t pos = 0, off = 0;
-  for (int t = 0; t < n_tensors; ++t) {
-    if (ndims[t] < 0 || ndims[t] > tnk::kMaxDims)
-      return fail(c, TN_ESHAPE, "tensor " + std::to_string(t) + ": bad number of bonds");
-    double sz = 1.0;
-    int64_t isz = 1;
-    for (int a = 0; a < ndims[t]; ++a) {
-      int b = bond_ids[pos++];
-      if (b < 0 || b >= n_bonds)
-        return fail(c, TN_ESHAPE, "tensor " + std::to_string(t) + ": bond id out of range");
-      if (first[b] == t)
-        return fail(c, TN_ESHAPE, "tensor " + std::to_string(t) + " lists bond " + std::to_string(b) + " twice");
-      if (first[b] < 0) first[b] = t;
-      count[b]++;
-      st->bonds[t].push_back(b);
-      sz *= (double)st->bond_dims[b];
-      isz *= st->bond_dims[b];
-    }
-    if (sz > 4e9) return fail(c, TN_ESHAPE, "tensor " + std::to_string(t) + " too large");
-    st->in_off[t] = off;
-    off += (isz + 31) / 32 * 32;
-  }
-  for (int b = 0; b < n_bonds; ++b)
-    if (count[b] != 2)
-      return fail(c, TN_ESHAPE,
-                  "bond " + std::to_string(b) + " appears " + std::to_string(count[b]) + " times (need 2)");
-  st->in_total = off;
-  return TN_OK;
+  std::string msg;
+  const int rc = tnx::check_structure(n_bonds, bond_dims, n_tensors, ndims, bond_ids, st, &msg);
+  return rc == TN_OK ? TN_OK : fail(c, rc, msg);
 }
 
 uint64_t structure_hash(const tnp::Structure& st) {
@@ -415,17 +384,21 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   if (before[0] != c->arena || before[1] != c->inbuf || before[2] != c->expo || before[3] != c->ginbuf ||
       before[4] != c->etape)
     drop_graphs(c);
-  tnk::DevState ds{c->expo, c->status};
-  unsigned long long* sw32 = c->profile ? c->sweeps : nullptr;
-  unsigned long long* sw64 = c->profile ? c->sweeps + 1 : nullptr;
-  auto ptr = [&](const tnp::PView& v) -> double* {
-    double* base = v.buf == tnp::BUF_INPUT ? c->inbuf + v.off
-                   : v.buf == tnp::BUF_GIN ? c->ginbuf + v.off
-                                           : c->arena + v.off * batch;
-    return base + v.eo;
-  };
-  auto cview = [&](const tnp::PView& v) { return tnk::View{ptr(v), v.rs, v.cs, v.bs}; };
-  auto wview = [&](const tnp::PView& v) { return tnk::ViewW{ptr(v), v.rs, v.cs, v.bs}; };
+  tnx::ExecEnv env;
+  env.inbuf = c->inbuf;
+  env.arena = c->arena;
+  env.ginbuf = c->ginbuf;
+  env.batch = batch;
+  env.ds = tnk::DevState{c->expo, c->status};
+  env.jac_ws = c->jac_ws;
+  env.maxbits = c->maxbits;
+  env.out_log = c->out_log;
+  env.out_sign = c->out_sign;
+  env.tc_err = c->tc_err;
+  env.etape = c->etape;
+  env.sweeps32 = c->profile ? c->sweeps : nullptr;
+  env.sweeps64 = c->profile ? c->sweeps + 1 : nullptr;
+  env.jac_max_sweeps = c->opt_max_sweeps;
 
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
   std::vector<int> ev_family;
@@ -466,82 +439,7 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);
     }
-    switch (stp.kind) {
-      case tnp::ST_PERMUTE:
-        e = tnk::permute_f64(ptr(stp.src), stp.src.bs, ptr(stp.dst), stp.dst.bs, (int)stp.in_dims.size(),
-                             stp.in_dims.data(), stp.perm.data(), batch, s);
-        break;
-      case tnp::ST_GEMM:
-        e = tnk::gemm_f64(stp.m, stp.n, stp.k, stp.alpha, cview(stp.A), cview(stp.B), stp.beta, wview(stp.C),
-                          batch, s);
-        break;
-      case tnp::ST_QR:
-        e = tnk::qr_r_f64(stp.m, stp.n, cview(stp.A), ptr(stp.work), stp.work.bs, wview(stp.C), batch, s);
-        break;
-      case tnp::ST_JACOBI:
-        e = tnk::jacobi_svd_f64(stp.m, stp.n, ptr(stp.C), stp.C.bs, stp.no_v ? nullptr : ptr(stp.aux1), stp.aux1.bs,
-                                ptr(stp.aux2), stp.aux2.bs, c->jac_ws, ds, stp.init_v, batch, s, sw64,
-                                stp.jac_tol);
-        break;
-      case tnp::ST_TO_F32:
-        e = tnk::convert_f64_to_f32(ptr(stp.src), stp.count, stp.src.bs, reinterpret_cast<float*>(ptr(stp.dst)),
-                                    stp.fbs_dst, batch, s);
-        break;
-      case tnp::ST_JACOBI32:
-        e = tnk::jacobi_svd_f32(stp.m, stp.n, reinterpret_cast<float*>(ptr(stp.C)), stp.fbs_src,
-                                reinterpret_cast<float*>(ptr(stp.aux1)), stp.fbs_dst, c->jac_ws, ds, batch, s, sw32);
-        break;
-      case tnp::ST_COPY:
-        e = cudaMemcpyAsync(ptr(stp.dst), ptr(stp.src), sizeof(double) * (size_t)stp.dst.bs * batch,
-                            cudaMemcpyDeviceToDevice, s);
-        break;
-      case tnp::ST_TO_F64:
-        e = tnk::convert_f32_to_f64(reinterpret_cast<const float*>(ptr(stp.src)), stp.count, stp.fbs_src,
-                                    ptr(stp.dst), ptr(stp.out1), stp.dst.bs, batch, s);
-        break;
-      case tnp::ST_SELECT:
-        e = tnk::select_scale_f64(stp.m, stp.n, stp.k, ptr(stp.C), stp.C.bs, stp.no_v ? nullptr : ptr(stp.aux1),
-                                  stp.aux1.bs,
-                                  ptr(stp.aux2), stp.aux2.bs, ptr(stp.out1), stp.out1.bs, (int)stp.count,
-                                  ptr(stp.out2), stp.out2.bs, stp.init_v, batch, s,
-                                  stp.no_v ? ptr(stp.work) : nullptr, stp.work.bs);
-        break;
-      case tnp::ST_APPLYQ:
-        e = tnk::apply_q_f64(stp.m, stp.n, ptr(stp.work), stp.work.bs, ptr(stp.C), stp.C.bs, stp.k, batch, s,
-                             stp.flag);
-        break;
-      case tnp::ST_GEMM_TC:
-        e = tnk::gemm_tc(stp.m, stp.n, stp.k, 1.0, cview(stp.A), cview(stp.B), wview(stp.C), batch, stp.tc_mode,
-                         ptr(stp.work), sizeof(double) * (size_t)stp.work.bs * batch, c->tc_err, s);
-        break;
-      case tnp::ST_RESCALE:
-        e = tnk::rescale_f64(ptr(stp.C), stp.count, stp.C.bs, c->maxbits, ds, batch, s,
-                             stp.slot >= 0 ? c->etape + (size_t)stp.slot * batch : nullptr);
-        break;
-      case tnp::ST_FINAL:
-        e = tnk::finalize_f64(ptr(stp.C), stp.C.bs, ds, c->out_log, c->out_sign, batch, s);
-        break;
-      case tnp::ST_SCALE_POW2:
-        e = tnk::scale_pow2_f64(ptr(stp.C), stp.count, stp.C.bs, c->etape + (size_t)stp.slot * batch, batch, s);
-        break;
-      case tnp::ST_FINAL_GRAD:
-        e = tnk::final_grad_f64(ptr(stp.C), stp.C.bs, ptr(stp.out1), stp.out1.bs, batch, s);
-        break;
-      case tnp::ST_SVD_FACTORS:
-        e = tnk::svd_factors_f64(stp.m, stp.n, stp.k, stp.flag, ptr(stp.C), stp.C.bs, ptr(stp.aux1), stp.aux1.bs,
-                                 ptr(stp.aux2), stp.aux2.bs, ptr(stp.out1), stp.out1.bs, ptr(stp.out2), stp.out2.bs,
-                                 ptr(stp.work), stp.work.bs, ptr(stp.A), stp.A.bs, ptr(stp.B), stp.B.bs, batch, s);
-        break;
-      case tnp::ST_SVD_ADJ_CORE:
-        e = tnk::svd_adjoint_core_f64(stp.n, stp.k, ptr(stp.A), stp.A.bs, ptr(stp.B), stp.B.bs, ptr(stp.work),
-                                      stp.work.bs, ptr(stp.C), stp.C.bs, batch, s);
-        break;
-      case tnp::ST_COPY2D:
-        e = tnk::copy2d_f64(stp.m, stp.n, cview(stp.A), wview(stp.C), batch, s);
-        break;
-      default:
-        e = cudaErrorInvalidValue;
-    }
+    e = tnx::exec_step(stp, env, s);
     if (e != cudaSuccess) {
       return fail(c, TN_ECUDA, std::string("launch of ") + kFamily[stp.kind] + " (tree op " +
                                    std::to_string(stp.op_index) + ") failed: " + cudaGetErrorString(e));
@@ -637,14 +535,34 @@ extern "C" {
 
 const char* tn_version(void) { return "tn-gb300 0.1"; }
 
-int tn_create(tn_ctx** out, int device) {
+void tn_options_default(tn_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->struct_size = (int32_t)sizeof(tn_options);
+  opt->graph_mode = 1;
+}
+
+int tn_create(tn_ctx** out, int device, const tn_options* opt) {
   if (!out) return TN_EINVAL;
   *out = nullptr;
+  tn_options o;
+  tn_options_default(&o);
+  if (opt) {
+    if (opt->struct_size < (int32_t)sizeof(tn_options)) return TN_EINVAL;
+    o = *opt;
+  }
+  if (o.graph_mode < 0 || o.graph_mode > 1 || o.grad_segments < 0 || o.debug_max_sweeps < 0 ||
+      !(o.tape_budget_bytes >= 0.0))
+    return TN_EINVAL;
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TN_ECUDA;
   tn_ctx* c = new (std::nothrow) tn_ctx();
   if (!c) return TN_ENOMEM;
   c->device = device;
+  c->graph_mode = o.graph_mode;
+  c->grad_segments = o.grad_segments;
+  c->tape_budget = o.tape_budget_bytes;
+  c->opt_max_sweeps = o.debug_max_sweeps;
   *out = c;
   return TN_OK;
 }
@@ -868,7 +786,7 @@ int tn_grad(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, doubl
     const tnp::Plan* plan = get_plan(c, inst_ids[q], chi, prec, &rc, segs);
     if (!plan) return rc;
     if (c->grad_segments == 0) {
-      // the whole tape does not fit in half the free device memory: checkpoint
+      // the whole tape does not fit in the budget (default half the free device memory): checkpoint
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
         cudaGetLastError();
@@ -876,7 +794,8 @@ int tn_grad(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, doubl
       }
       const double need = 8.0 * (double)plan->arena_units * (double)members.size();
       const size_t nops = c->insts[inst_ids[q]].ops.size() / 4;
-      if (free_b && need > 0.5 * (double)free_b && nops > 1) {
+      const double budget = c->tape_budget > 0.0 ? c->tape_budget : 0.5 * (double)free_b;
+      if ((c->tape_budget > 0.0 || free_b) && need > budget && nops > 1) {
         segs = (int)std::ceil(std::sqrt((double)nops));
         plan = get_plan(c, inst_ids[q], chi, prec, &rc, segs);
         if (!plan) return rc;

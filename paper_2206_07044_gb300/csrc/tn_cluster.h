@@ -14,21 +14,24 @@
 
 namespace tnk {
 
-// Runs set(), which sets function attributes, once per (key, device): CUDA
-// function attributes belong to the device's context, so a process that uses
-// several GPUs must set them on each.
+// Runs set(), which sets function attributes and returns a cudaError_t, once
+// per (key, device): CUDA function attributes belong to the device's context,
+// so a process that uses several GPUs must set them on each.  A pair is marked
+// done only when set() succeeded (a failure is retried on the next launch and
+// returned to the caller, who reports it as a launch error).
 template <typename F>
-inline void once_per_device(const void* key, F set) {
+inline cudaError_t once_per_device(const void* key, F set) {
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, bool> done;
   int dev = 0;
-  cudaGetDevice(&dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
   bool& d = done[{key, dev}];
-  if (!d) {
-    set();
-    d = true;
-  }
+  if (d) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess) d = true;
+  return e;
 }
 
 // Clusters of `cluster` CTAs (threads, dynamic smem bytes) of kernel `func` that

@@ -45,11 +45,12 @@ cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW 
 // accumulated rotations (V = I first when init_v), sig the FP64 column norms
 // sigma_i (unsorted).  ws: 64 ints per batch of scratch.  Sets st.status[b] = -9
 // if the bounded sweep loop ran out.
-// sweep_ctr (optional, device): the sweeps run are added to it.
+// sweep_ctr (optional, device): the sweeps run are added to it.  max_sweeps
+// caps the sweep loop (0: 60 sweeps).
 cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int64_t v_bs,
                            double* sig, int64_t sig_bs, int* ws, DevState st, int init_v,
                            int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr,
-                           double sig_tol = 1e-8);
+                           double sig_tol = 1e-8, int max_sweeps = 0);
 // The FP32 preconditioning pass (V = I first); never sets a status.
 cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64_t v_bs, int* ws,
                            DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr);

@@ -10,7 +10,9 @@
 // result words -- from one file-scope __device__ array of fixed size
 // (kNoAllocBytes below, 8 MiB), which every GPU that loads the library holds
 // until the process exits.  The kernels, the schedule and therefore the
-// results are the same as tn_contract_approx's for a batch of one.
+// results are the same as tn_contract_approx's for a batch of one in the FP64
+// form with the plain Q-form compressions; the network checks and the launch
+// of every step are the shared ones of tn_exec.cpp.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +24,7 @@
 #include <vector>
 
 #include "../../include/tn.h"
+#include "tn_exec.h"
 #include "tn_kernels.h"
 #include "tn_plan.h"
 
@@ -51,40 +54,22 @@ extern "C" int tn_contract_approx_noalloc(const tn_network_desc* net, const tn_t
                                           size_t err_cap) {
   if (!net || !tree || !logabsz_out || !sign_out) return set_err(err_msg, err_cap, TN_EINVAL, "NULL argument");
   if (chi < 1) return set_err(err_msg, err_cap, TN_EINVAL, "chi must be >= 1");
-  if (net->n_tensors < 1 || net->n_bonds < 0 || !net->ndims || !net->data || (net->n_bonds > 0 && !net->bond_dims))
-    return set_err(err_msg, err_cap, TN_EINVAL, "bad network descriptor");
-  // structure and validation (every bond in exactly two tensors, finite entries)
+  if (!net->data) return set_err(err_msg, err_cap, TN_EINVAL, "data is NULL");
+  // the same structure checks as tn_load_network (every bond in exactly two
+  // different tensors, sizes in range), then the same finite-entry scan
   tnp::Structure st;
-  st.bond_dims.assign(net->bond_dims, net->bond_dims + net->n_bonds);
-  std::vector<int> count(net->n_bonds, 0);
-  int64_t pos = 0, off = 0;
+  std::string why;
+  const int src = tnx::check_structure(net->n_bonds, net->bond_dims, net->n_tensors, net->ndims, net->bond_ids, &st,
+                                       &why);
+  if (src != TN_OK) return set_err(err_msg, err_cap, src, why);
   for (int t = 0; t < net->n_tensors; ++t) {
-    if (net->ndims[t] < 0 || net->ndims[t] > tnk::kMaxDims)
-      return set_err(err_msg, err_cap, TN_ESHAPE, "tensor " + std::to_string(t) + ": bad number of bonds");
-    std::vector<int> bl;
-    int64_t size = 1;
-    for (int a = 0; a < net->ndims[t]; ++a) {
-      const int b = net->bond_ids[pos++];
-      if (b < 0 || b >= net->n_bonds || net->bond_dims[b] < 1)
-        return set_err(err_msg, err_cap, TN_ESHAPE, "tensor " + std::to_string(t) + ": bad bond");
-      for (int x : bl)
-        if (x == b) return set_err(err_msg, err_cap, TN_ESHAPE, "a tensor lists a bond twice");
-      bl.push_back(b);
-      count[b]++;
-      size *= net->bond_dims[b];
-      if (size > (int64_t(1) << 40)) return set_err(err_msg, err_cap, TN_ESHAPE, "tensor too large");
-    }
     if (!net->data[t]) return set_err(err_msg, err_cap, TN_EINVAL, "tensor data pointer is NULL");
+    int64_t size = 1;
+    for (int b : st.bonds[t]) size *= st.bond_dims[b];
     for (int64_t i = 0; i < size; ++i)
       if (!std::isfinite(net->data[t][i]))
         return set_err(err_msg, err_cap, TN_ENONFINITE, "tensor " + std::to_string(t) + " has a non-finite entry");
-    st.bonds.push_back(bl);
-    st.in_off.push_back(off);
-    off += (size + 31) / 32 * 32;
   }
-  for (int b = 0; b < net->n_bonds; ++b)
-    if (count[b] != 2) return set_err(err_msg, err_cap, TN_ESHAPE, "bond " + std::to_string(b) + " is not shared by two tensors");
-  st.in_total = off;
   if (tree->n_ops < 0 || (tree->n_ops > 0 && !tree->ops)) return set_err(err_msg, err_cap, TN_EINVAL, "bad tree");
   std::vector<int32_t> ops(tree->ops, tree->ops + 4 * (size_t)tree->n_ops);
   for (int32_t q = 0; q < tree->n_ops; ++q)
@@ -98,7 +83,7 @@ extern "C" int tn_contract_approx_noalloc(const tn_network_desc* net, const tn_t
   const size_t in_bytes = up(sizeof(double) * (size_t)std::max<int64_t>(st.in_total, 1));
   const size_t arena_bytes = up(sizeof(double) * (size_t)std::max<int64_t>(plan.arena_units, 1));
   const size_t word_bytes = up(sizeof(long long)) + up(sizeof(int)) + up(sizeof(int) * 64) +
-                            up(sizeof(unsigned long long)) + up(sizeof(double)) + up(sizeof(int));
+                            up(sizeof(unsigned long long)) + up(sizeof(double)) + up(sizeof(int)) + up(sizeof(int));
   const size_t need = in_bytes + arena_bytes + word_bytes;
   if (need > kNoAllocBytes)
     return set_err(err_msg, err_cap, TN_ENOMEM,
@@ -134,6 +119,8 @@ extern "C" int tn_contract_approx_noalloc(const tn_network_desc* net, const tn_t
   double* out_log = reinterpret_cast<double*>(w);
   w += up(sizeof(double));
   int* out_sign = reinterpret_cast<int*>(w);
+  w += up(sizeof(int));
+  int* tc_err = reinterpret_cast<int*>(w);
 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t ce = cudaSuccess;
@@ -145,65 +132,20 @@ extern "C" int tn_contract_approx_noalloc(const tn_network_desc* net, const tn_t
   // the array keeps the previous call's contents: zero what must start at zero
   if (ce == cudaSuccess) ce = cudaMemsetAsync(expo, 0, sizeof(long long), s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(status, 0, sizeof(int), s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(tc_err, 0, sizeof(int), s);
   if (ce != cudaSuccess) return set_err(err_msg, err_cap, TN_ECUDA, std::string("upload: ") + cudaGetErrorString(ce));
-  tnk::DevState ds{expo, status};
-  auto ptr = [&](const tnp::PView& v) -> double* {
-    return (v.buf == tnp::BUF_INPUT ? inbuf + v.off : arena + v.off) + v.eo;
-  };
-  auto cview = [&](const tnp::PView& v) { return tnk::View{ptr(v), v.rs, v.cs, v.bs}; };
-  auto wview = [&](const tnp::PView& v) { return tnk::ViewW{ptr(v), v.rs, v.cs, v.bs}; };
-  const int batch = 1;
+  tnx::ExecEnv env;
+  env.inbuf = inbuf;
+  env.arena = arena;
+  env.batch = 1;
+  env.ds = tnk::DevState{expo, status};
+  env.jac_ws = jac_ws;
+  env.maxbits = maxbits;
+  env.out_log = out_log;
+  env.out_sign = out_sign;
+  env.tc_err = tc_err;
   for (const tnp::Step& stp : plan.steps) {
-    switch (stp.kind) {
-      case tnp::ST_PERMUTE:
-        ce = tnk::permute_f64(ptr(stp.src), stp.src.bs, ptr(stp.dst), stp.dst.bs, (int)stp.in_dims.size(),
-                              stp.in_dims.data(), stp.perm.data(), batch, s);
-        break;
-      case tnp::ST_GEMM:
-        ce = tnk::gemm_f64(stp.m, stp.n, stp.k, stp.alpha, cview(stp.A), cview(stp.B), stp.beta, wview(stp.C),
-                           batch, s);
-        break;
-      case tnp::ST_QR:
-        ce = tnk::qr_r_f64(stp.m, stp.n, cview(stp.A), ptr(stp.work), stp.work.bs, wview(stp.C), batch, s);
-        break;
-      case tnp::ST_JACOBI:
-        ce = tnk::jacobi_svd_f64(stp.m, stp.n, ptr(stp.C), stp.C.bs, stp.no_v ? nullptr : ptr(stp.aux1), stp.aux1.bs, ptr(stp.aux2),
-                                 stp.aux2.bs, jac_ws, ds, stp.init_v, batch, s);
-        break;
-      case tnp::ST_SELECT:
-        ce = tnk::select_scale_f64(stp.m, stp.n, stp.k, ptr(stp.C), stp.C.bs, stp.no_v ? nullptr : ptr(stp.aux1), stp.aux1.bs,
-                                   ptr(stp.aux2), stp.aux2.bs, ptr(stp.out1), stp.out1.bs, (int)stp.count,
-                                   ptr(stp.out2), stp.out2.bs, stp.init_v, batch, s,
-                                   stp.no_v ? ptr(stp.work) : nullptr, stp.work.bs);
-        break;
-      case tnp::ST_APPLYQ:
-        ce = tnk::apply_q_f64(stp.m, stp.n, ptr(stp.work), stp.work.bs, ptr(stp.C), stp.C.bs, stp.k, batch, s);
-        break;
-      case tnp::ST_RESCALE:
-        ce = tnk::rescale_f64(ptr(stp.C), stp.count, stp.C.bs, maxbits, ds, batch, s);
-        break;
-      case tnp::ST_FINAL:
-        ce = tnk::finalize_f64(ptr(stp.C), stp.C.bs, ds, out_log, out_sign, batch, s);
-        break;
-      case tnp::ST_TO_F32:
-        ce = tnk::convert_f64_to_f32(ptr(stp.src), stp.count, stp.src.bs, reinterpret_cast<float*>(ptr(stp.dst)),
-                                     stp.fbs_dst, batch, s);
-        break;
-      case tnp::ST_JACOBI32:
-        ce = tnk::jacobi_svd_f32(stp.m, stp.n, reinterpret_cast<float*>(ptr(stp.C)), stp.fbs_src,
-                                 reinterpret_cast<float*>(ptr(stp.aux1)), stp.fbs_dst, jac_ws, ds, batch, s);
-        break;
-      case tnp::ST_TO_F64:
-        ce = tnk::convert_f32_to_f64(reinterpret_cast<const float*>(ptr(stp.src)), stp.count, stp.fbs_src,
-                                     ptr(stp.dst), ptr(stp.out1), stp.dst.bs, batch, s);
-        break;
-      case tnp::ST_COPY:
-        ce = cudaMemcpyAsync(ptr(stp.dst), ptr(stp.src), sizeof(double) * (size_t)stp.dst.bs,
-                             cudaMemcpyDeviceToDevice, s);
-        break;
-      default:
-        ce = cudaErrorInvalidValue;
-    }
+    ce = tnx::exec_step(stp, env, s);
     if (ce != cudaSuccess) return set_err(err_msg, err_cap, TN_ECUDA, std::string("launch: ") + cudaGetErrorString(ce));
   }
   double lg = 0.0;

@@ -46,10 +46,16 @@ class PlanStats(C.Structure):
                 ("kernel_launches", C.c_int64)]
 
 
+class Options(C.Structure):
+    _fields_ = [("struct_size", C.c_int32), ("graph_mode", C.c_int32), ("grad_segments", C.c_int32),
+                ("debug_max_sweeps", C.c_int32), ("tape_budget_bytes", C.c_double)]
+
+
 # every symbol include/tn.h declares, with its ctypes signature
 SIGNATURES = {
     "tn_version": (C.c_char_p, []),
-    "tn_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
+    "tn_options_default": (None, [C.POINTER(Options)]),
+    "tn_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(Options)]),
     "tn_destroy": (None, [C.c_void_p]),
     "tn_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tn_set_graph_mode": (C.c_int, [C.c_void_p, C.c_int]),
@@ -144,10 +150,18 @@ def _stream_handle(stream) -> int:
 class Context:
     """One library context on one CUDA device."""
 
-    def __init__(self, device: int = 0, stream=None):
+    def __init__(self, device: int = 0, stream=None, **options):
+        """options: any field of tn_options (graph_mode, grad_segments,
+        tape_budget_bytes, debug_max_sweeps); the rest keep their defaults."""
         self._L = lib()
+        opt = Options()
+        self._L.tn_options_default(C.byref(opt))
+        for k, v in options.items():
+            if k == "struct_size" or k not in dict(Options._fields_):
+                raise TypeError(f"unknown tn_options field {k!r}")
+            setattr(opt, k, v)
         h = C.c_void_p()
-        rc = self._L.tn_create(C.byref(h), int(device))
+        rc = self._L.tn_create(C.byref(h), int(device), C.byref(opt))
         if rc != 0:
             raise TNError(rc, f"tn_create(device={device}) failed (no CUDA device?)")
         self._h = h

@@ -43,7 +43,19 @@ def test_version_and_null_handling(libpath):
     L = tn.lib()
     assert L.tn_version().decode().startswith("tn-gb300")
     assert L.tn_last_error(None) == b"NULL context"
-    assert L.tn_create(None, 0) == -1           # TN_EINVAL on a NULL out-pointer
+    assert L.tn_create(None, 0, None) == -1     # TN_EINVAL on a NULL out-pointer
+    opt = tn.Options()
+    L.tn_options_default(ctypes.byref(opt))
+    assert opt.struct_size == ctypes.sizeof(tn.Options) and opt.graph_mode == 1
+    assert opt.grad_segments == 0 and opt.debug_max_sweeps == 0 and opt.tape_budget_bytes == 0.0
+    h = ctypes.c_void_p()
+    bad = tn.Options()
+    L.tn_options_default(ctypes.byref(bad))
+    bad.struct_size = 4                         # an options struct older than the first version
+    assert L.tn_create(ctypes.byref(h), 0, ctypes.byref(bad)) == -1
+    L.tn_options_default(ctypes.byref(bad))
+    bad.debug_max_sweeps = -1
+    assert L.tn_create(ctypes.byref(h), 0, ctypes.byref(bad)) == -1
     L.tn_destroy(None)                          # ignored
 
 
