@@ -119,13 +119,21 @@ typedef struct {
  *   debug_max_sweeps   > 0: cap the FP64 Jacobi sweep loop of every core
  *                      SVD at this many sweeps (a matrix that needs more
  *                      makes the call return TN_ENOCONV); 0: 60 sweeps.
- *                      For tests of the bounded loop; leave 0 otherwise. */
+ *                      For tests of the bounded loop; leave 0 otherwise.
+ *   debug_tc_give_up   1: the pipeline waits of the tensor-core GEMM (mixed
+ *                      forms) give up without polling, as if their poll
+ *                      budget had run out: each such GEMM drains its copies
+ *                      in flight, releases its TMEM and flags the call,
+ *                      which returns TN_ETIMEOUT.  For tests of the bounded
+ *                      waits; leave 0 otherwise. */
 typedef struct {
   int32_t struct_size;
   int32_t graph_mode;
   int32_t grad_segments;
   int32_t debug_max_sweeps;
   double tape_budget_bytes;
+  int32_t debug_tc_give_up;
+  int32_t reserved;
 } tn_options;
 
 /* Default options (struct_size = sizeof(tn_options)). */
@@ -133,7 +141,7 @@ void tn_options_default(tn_options* opt);
 
 /* Create a context on CUDA device `device` with options `opt` (NULL: the
  * defaults).  *out receives the context.  Errors: TN_EINVAL (NULL out, a
- * struct_size smaller than the first version's, negative fields), TN_ECUDA
+ * struct_size smaller than this version's, fields out of range), TN_ECUDA
  * (no such device). */
 int tn_create(tn_ctx** out, int device, const tn_options* opt);
 
@@ -284,7 +292,11 @@ int tn_plan_stats_get(tn_ctx* ctx, int inst_id, int chi, int prec, tn_plan_stats
  * by compressions, numbered in execution order.  out == NULL queries the
  * shape only and runs nothing.  TN_EINVAL if the tensor does not exist after
  * that op.  Intermediates carry the running power-of-two scale, so values
- * equal the exact ones up to a factor 2^e. */
+ * equal the exact ones up to a factor 2^e.  Consecutive calls on the same
+ * batch and plan with non-decreasing stop_op (and no other work on the
+ * context in between) continue from where the previous call stopped instead
+ * of re-running the schedule from the start; the pass is deterministic, so
+ * the tensors are the same as from a fresh run. */
 int tn_debug_tensor(tn_ctx* ctx, int n_inst, const int* inst_ids, int which, int chi, int prec,
                     int stop_op, int tensor_id, double* out, int64_t cap, int32_t* ndim_out,
                     int32_t* bond_ids_out, int64_t* dims_out);

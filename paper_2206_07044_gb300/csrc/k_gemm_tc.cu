@@ -16,8 +16,14 @@
 //                   tcgen05.commit frees each stage / signals the epilogue;
 //   warps 0-3       read the accumulator with tcgen05.ld (lane = row) and
 //                   write alpha * D to C in FP64.
-// Every mbarrier wait is bounded: after kSpinLimit polls the kernel records an
-// error in *err, skips its remaining work and still releases its TMEM.
+// Every mbarrier wait is bounded: after a poll budget the kernel records an
+// error in *err, skips its remaining work and still releases its TMEM.  The
+// pipeline waits (a free stage for the producer, a loaded stage for the MMA
+// issuer) use `pipe_spin` polls (kSpinLimit normally; 0 when a test asks the
+// kernel to give up at once); the drain waits that must end before the CTA
+// exits -- the TMA copies still in flight, the MMAs still writing TMEM --
+// always use kSpinLimit, so an early give-up never leaves asynchronous work
+// running behind an exited CTA.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -50,10 +56,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait on phase `parity`; returns false if the poll budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait on phase `parity`; returns false if `limit` polls ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -95,7 +101,8 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc_kernel(const __grid_consta
                                                              const __grid_constant__ CUtensorMap mapB, int m,
                                                              int n, int kblocks, double alpha, ViewW C,
                                                              int64_t a_rows_per_batch, int64_t b_rows_per_batch,
-                                                             int64_t a_lo_row, int64_t b_lo_row, int* err) {
+                                                             int64_t a_lo_row, int64_t b_lo_row, int* err,
+                                                             uint32_t pipe_spin) {
   constexpr bool kBF16 = (kMode == 1);
   constexpr bool kSplit = (kMode == 2);
   constexpr int kStages = kSplit ? 3 : ::tnk::kStages;
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc_kernel(const __grid_consta
     for (int kb = 0; kb < kblocks; ++kb) {
       const int s = kb % kStages;
       if (kb >= kStages) {
-        if (!mbar_wait(&empty_bar[s], ((kb / kStages) - 1) & 1)) {
+        if (!mbar_wait(&empty_bar[s], ((kb / kStages) - 1) & 1, pipe_spin)) {
           atomicExch(&abort_flag, 1);
           break;
         }
@@ -164,16 +171,19 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc_kernel(const __grid_consta
       }
       issued = kb + 1;
     }
-    // on an abort, wait (bounded) for the copies still in flight before the CTA exits
-    if (abort_flag) {
-      for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
-        mbar_wait(&full_bar[kb % kStages], (kb / kStages) & 1);
-    }
+    // Before the CTA can exit, every copy issued must have landed.  The last
+    // kStages loads are the only ones the MMA issuer may not have waited for
+    // (it can lag by at most the ring's depth), so wait for exactly those, on
+    // every path: after a normal run they completed long ago and the test
+    // returns at once; after a give-up on either side (possibly decided after
+    // this loop ended) they may still be in flight.
+    for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
+      mbar_wait(&full_bar[kb % kStages], (kb / kStages) & 1);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     for (int kb = 0; kb < kblocks; ++kb) {
       const int s = kb % kStages;
-      if (!mbar_wait(&full_bar[s], (kb / kStages) & 1)) {
+      if (!mbar_wait(&full_bar[s], (kb / kStages) & 1, pipe_spin)) {
         atomicExch(&abort_flag, 1);
         break;
       }
@@ -320,7 +330,7 @@ bool make_map(CUtensorMap* map, void* ptr, bool bf16, int64_t rows, int64_t kp, 
 template <int kMode, int BN>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int m, int n, int kblocks, double alpha,
                       ViewW C, int64_t arows, int64_t brows, int64_t alo, int64_t blo, int tiles_m, int tiles_n,
-                      int batch, int* err, cudaStream_t s) {
+                      int batch, int* err, cudaStream_t s, uint32_t pipe_spin) {
   const int stages = kMode == 2 ? 3 : kStages;
   const int split = kMode == 2 ? 2 : 1;
   const size_t smem = 1024 + (size_t)stages * split * (kBM * 128 + BN * 128);
@@ -330,7 +340,7 @@ cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int m, int n
   if (ae != cudaSuccess) return ae;
   dim3 grid(tiles_n, tiles_m, batch);
   gemm_tc_kernel<kMode, BN><<<grid, kTcThreads, smem, s>>>(ma, mb, m, n, kblocks, alpha, C, arows, brows, alo, blo,
-                                                           err);
+                                                           err, pipe_spin);
   return cudaGetLastError();
 }
 
@@ -351,8 +361,9 @@ size_t gemm_tc_workspace_bytes(int m, int n, int k, int mode, int batch) {
 }
 
 cudaError_t gemm_tc(int m, int n, int k, double alpha, View A, View B, ViewW C, int batch, int mode,
-                    void* workspace, size_t ws_bytes, int* err, cudaStream_t s) {
+                    void* workspace, size_t ws_bytes, int* err, cudaStream_t s, bool give_up_at_once) {
   if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
+  const uint32_t spin = give_up_at_once ? 0u : kSpinLimit;
   if (mode < 0 || mode > 2) return cudaErrorInvalidValue;
   if (batch > 65535 || ws_bytes < gemm_tc_workspace_bytes(m, n, k, mode, batch)) return cudaErrorInvalidValue;
   const bool bf16 = mode == 1;
@@ -396,17 +407,17 @@ cudaError_t gemm_tc(int m, int n, int k, double alpha, View A, View B, ViewW C, 
   const int tm = (int)(mp / kBM), tn = (int)(np / bn);
   const int64_t alo_row = mp * batch, blo_row = np * batch;
   if (mode == 2) {
-    if (bn == 64) return launch_tc<2, 64>(ma, mb, m, n, kblocks, alpha, C, mp, np, alo_row, blo_row, tm, tn, batch, err, s);
-    return launch_tc<2, 128>(ma, mb, m, n, kblocks, alpha, C, mp, np, alo_row, blo_row, tm, tn, batch, err, s);
+    if (bn == 64) return launch_tc<2, 64>(ma, mb, m, n, kblocks, alpha, C, mp, np, alo_row, blo_row, tm, tn, batch, err, s, spin);
+    return launch_tc<2, 128>(ma, mb, m, n, kblocks, alpha, C, mp, np, alo_row, blo_row, tm, tn, batch, err, s, spin);
   }
   if (bf16) {
-    if (bn == 64) return launch_tc<1, 64>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s);
-    if (bn == 128) return launch_tc<1, 128>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s);
-    return launch_tc<1, 256>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s);
+    if (bn == 64) return launch_tc<1, 64>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s, spin);
+    if (bn == 128) return launch_tc<1, 128>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s, spin);
+    return launch_tc<1, 256>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s, spin);
   }
-  if (bn == 64) return launch_tc<0, 64>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s);
-  if (bn == 128) return launch_tc<0, 128>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s);
-  return launch_tc<0, 256>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s);
+  if (bn == 64) return launch_tc<0, 64>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s, spin);
+  if (bn == 128) return launch_tc<0, 128>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s, spin);
+  return launch_tc<0, 256>(ma, mb, m, n, kblocks, alpha, C, mp, np, 0, 0, tm, tn, batch, err, s, spin);
 }
 
 }  // namespace tnk

@@ -73,7 +73,8 @@ struct GraphRec {
 
 const char* kFamily[] = {"permute", "gemm_f64",   "qr_f64",     "jacobi_f64",  "select_scale", "rescale",
                          "finalize", "to_f32",     "jacobi_f32", "to_f64",      "copy",         "apply_q_f64",
-                         "gemm_tc",  "scale_pow2", "final_grad", "svd_factors", "svd_adj_core", "copy2d"};
+                         "gemm_tc",  "scale_pow2", "final_grad", "svd_factors", "svd_adj_core", "copy2d",
+                         "mark_active"};
 static_assert(sizeof(kFamily) / sizeof(kFamily[0]) == tnp::kNumStepKinds, "one family name per step kind");
 constexpr int kNumFamily = tnp::kNumStepKinds;
 
@@ -115,11 +116,17 @@ struct tn_ctx {
   int gauge_r = -1;       // compressions in the tree gauge of this distance (-1: plain Q-form)
   double tape_budget = 0.0;  // tn_grad: tape bytes before checkpointing (0: half the free device memory)
   int opt_max_sweeps = 0;    // > 0: FP64 Jacobi sweep cap (tests of the bounded loop)
+  bool opt_tc_give_up = false;  // tests: tensor-core GEMM pipeline waits give up at once
   uint64_t plan_serial = 0;
   uint64_t buf_gen = 0;  // bumped whenever a buffer a captured graph points into moves
   cudaStream_t cap = nullptr;
   std::map<GraphKey, GraphRec> graphs;
   int64_t graph_captured = 0, graph_replays = 0, graph_refused = 0;
+  // tn_debug_tensor: where the last partial run stopped (its plan, members and
+  // buffer generation), so that a later call with a later stop continues from there
+  uint64_t dbg_serial = 0, dbg_gen = 0;
+  std::vector<int> dbg_members;
+  int dbg_stop = -2;  // -2: no partial run to continue
   // profiling
   bool profile = false;
   unsigned long long prof_sweeps[2] = {0, 0};
@@ -348,11 +355,15 @@ void capture_graph(tn_ctx* c, GraphRec* gr, F& enqueue) {
 
 // Run the plan on a batch.  With stop_op >= 0, only the steps of tree ops
 // 0..stop_op run (no final read-out) and the call returns after syncing; the
-// arena then holds every tensor alive after that op.
+// arena then holds every tensor alive after that op.  resume_after >= -1
+// (with stop_op >= 0): the device already holds the state after tree op
+// resume_after of this same plan and batch, so the input gather and the steps
+// of ops 0..resume_after are skipped.
 int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members, double* logabs,
-              int* sign, int stop_op = -1) {
+              int* sign, int stop_op = -1, int resume_after = -2) {
   const int batch = (int)members.size();
   if (batch > 65535) return fail(c, TN_EINVAL, "more than 65535 instances in one batch");
+  c->dbg_stop = -2;  // any run overwrites the state a partial debug run left
   const tnp::Structure& st = c->nets[c->insts[members[0]].net].st;
   cudaError_t e;
   const void* before[5] = {c->arena, c->inbuf, c->expo, c->ginbuf, c->etape};
@@ -399,6 +410,7 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   env.sweeps32 = c->profile ? c->sweeps : nullptr;
   env.sweeps64 = c->profile ? c->sweeps + 1 : nullptr;
   env.jac_max_sweeps = c->opt_max_sweeps;
+  env.tc_give_up = c->opt_tc_give_up;
 
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
   std::vector<int> ev_family;
@@ -408,19 +420,21 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   auto enqueue = [&](cudaStream_t s0) -> int {
   cudaStream_t s = s0;
   cudaError_t e = cudaSuccess;
-  for (int b = 0; b < batch && e == cudaSuccess; ++b) {
+  const bool resuming = stop_op >= 0 && resume_after >= -1;
+  for (int b = 0; b < batch && e == cudaSuccess && !resuming; ++b) {
     const NetRec& nr = c->nets[c->insts[members[b]].net];
     e = cudaMemcpyAsync(c->inbuf + (size_t)b * st.in_total, nr.d_data, sizeof(double) * st.in_total,
                         cudaMemcpyDeviceToDevice, s);
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->expo, 0, sizeof(long long) * batch, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int) * batch, s);
+  if (e == cudaSuccess && !resuming) e = cudaMemsetAsync(c->expo, 0, sizeof(long long) * batch, s);
+  if (e == cudaSuccess && !resuming) e = cudaMemsetAsync(c->status, 0, sizeof(int) * batch, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->tc_err, 0, sizeof(int), s);
   if (e == cudaSuccess && c->profile) e = cudaMemsetAsync(c->sweeps, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "gather inputs");
   bool side_open = false;
   for (const tnp::Step& stp : plan.steps) {
     if (stop_op >= 0 && (stp.op_index > stop_op || stp.kind == tnp::ST_FINAL)) break;
+    if (resuming && stp.op_index <= resume_after) continue;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (stp.join && side_open) {
       cudaStreamWaitEvent(s, c->ev_join, 0);
@@ -552,7 +566,7 @@ int tn_create(tn_ctx** out, int device, const tn_options* opt) {
     o = *opt;
   }
   if (o.graph_mode < 0 || o.graph_mode > 1 || o.grad_segments < 0 || o.debug_max_sweeps < 0 ||
-      !(o.tape_budget_bytes >= 0.0))
+      !(o.tape_budget_bytes >= 0.0) || o.debug_tc_give_up < 0 || o.debug_tc_give_up > 1)
     return TN_EINVAL;
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TN_ECUDA;
@@ -563,6 +577,7 @@ int tn_create(tn_ctx** out, int device, const tn_options* opt) {
   c->grad_segments = o.grad_segments;
   c->tape_budget = o.tape_budget_bytes;
   c->opt_max_sweeps = o.debug_max_sweeps;
+  c->opt_tc_give_up = o.debug_tc_give_up != 0;
   *out = c;
   return TN_OK;
 }
@@ -929,8 +944,21 @@ int tn_debug_tensor(tn_ctx* c, int n_inst, const int* inst_ids, int which, int c
   std::vector<int> members(inst_ids, inst_ids + n_inst);
   std::vector<double> lg(n_inst);
   std::vector<int> sg(n_inst);
-  rc = run_group(c, *plan, members, lg.data(), sg.data(), stop_op < 0 ? INT32_MAX : stop_op);
-  if (rc != TN_OK) return rc;
+  const int stop = stop_op < 0 ? INT32_MAX : stop_op;
+  // the previous call left this plan's state after op dbg_stop on the same batch: continue from there
+  const bool cont = c->dbg_stop >= -1 && c->dbg_serial == plan->serial && c->dbg_members == members &&
+                    c->dbg_gen == c->buf_gen && stop >= c->dbg_stop && stop != INT32_MAX;
+  if (!(cont && stop == c->dbg_stop)) {
+    const int prev = cont ? c->dbg_stop : -2;
+    rc = run_group(c, *plan, members, lg.data(), sg.data(), stop, prev);
+    if (rc != TN_OK) return rc;
+    if (stop != INT32_MAX) {
+      c->dbg_serial = plan->serial;
+      c->dbg_gen = c->buf_gen;
+      c->dbg_members = members;
+      c->dbg_stop = stop;
+    }
+  }
   const int batch = n_inst;
   const double* base = rec->view.buf == tnp::BUF_INPUT ? c->inbuf + rec->view.off : c->arena + rec->view.off * batch;
   cudaError_t e = cudaMemcpy(out, base + (int64_t)which * rec->view.bs, sizeof(double) * size, cudaMemcpyDeviceToHost);

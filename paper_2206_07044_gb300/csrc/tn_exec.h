@@ -30,6 +30,7 @@ struct ExecEnv {
   unsigned long long* sweeps32 = nullptr;  // optional Jacobi sweep counters
   unsigned long long* sweeps64 = nullptr;
   int jac_max_sweeps = 0;        // > 0: cap on the Jacobi sweep loops (0: the kernels' default)
+  bool tc_give_up = false;       // tests: the tensor-core GEMM's pipeline waits give up at once
 
   double* ptr(const tnp::PView& v) const {
     double* base = v.buf == tnp::BUF_INPUT ? inbuf + v.off

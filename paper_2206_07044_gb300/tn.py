@@ -48,7 +48,8 @@ class PlanStats(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("struct_size", C.c_int32), ("graph_mode", C.c_int32), ("grad_segments", C.c_int32),
-                ("debug_max_sweeps", C.c_int32), ("tape_budget_bytes", C.c_double)]
+                ("debug_max_sweeps", C.c_int32), ("tape_budget_bytes", C.c_double),
+                ("debug_tc_give_up", C.c_int32), ("reserved", C.c_int32)]
 
 
 # every symbol include/tn.h declares, with its ctypes signature
@@ -152,12 +153,13 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None, **options):
         """options: any field of tn_options (graph_mode, grad_segments,
-        tape_budget_bytes, debug_max_sweeps); the rest keep their defaults."""
+        tape_budget_bytes, debug_max_sweeps, debug_tc_give_up); the rest keep
+        their defaults."""
         self._L = lib()
         opt = Options()
         self._L.tn_options_default(C.byref(opt))
         for k, v in options.items():
-            if k == "struct_size" or k not in dict(Options._fields_):
+            if k in ("struct_size", "reserved") or k not in dict(Options._fields_):
                 raise TypeError(f"unknown tn_options field {k!r}")
             setattr(opt, k, v)
         h = C.c_void_p()

@@ -221,3 +221,31 @@ def test_grad_checkpointed_equals_one_tape(ctx):
     assert max_rel(g3[0], g1[0]) <= 1e-13
     want = grad.contract_with_grad(net, tree, 5)
     assert max_rel(g3[0], want.grads) <= GRAD_TOL
+
+
+def test_dlnz_dbeta_batched_sweep(ctx):
+    """Internal energy of a beta sweep from one tn_grad call (log_z_batch) equals the
+    per-instance wrapper and the oracle's reverse pass at every beta."""
+    import torch
+    from paper_2206_07044_gb300.autograd import log_z, log_z_batch
+    from tn_inputs import torch_ising as ti
+    n, e = nw.square_lattice(8, 8)
+    tree = tr.boundary_rows(8, 8)
+    betas = [0.3, 0.41, 0.44, 0.52, 0.65]
+    ids = [ctx.load_tree(ctx.load_network(nw.ising_network(n, e, b)), tree) for b in betas]
+    bt = [torch.tensor(b, dtype=torch.float64, requires_grad=True) for b in betas]
+    ones = torch.ones(len(e), dtype=torch.float64)
+    lz = log_z_batch(ctx, ids, [ti.ising_tensors(n, e, b, ones, True) for b in bt], 16)
+    assert lz.shape == (len(betas),)
+    lz.sum().backward()
+    for b, iid, bb, l in zip(betas, ids, bt, lz.detach()):
+        b1 = torch.tensor(b, dtype=torch.float64, requires_grad=True)
+        l1 = log_z(ctx, iid, ti.ising_tensors(n, e, b1, ones, True), 16)
+        l1.backward()
+        assert abs(float(l) - float(l1)) <= 1e-13 * abs(float(l1))
+        assert abs(float(bb.grad) - float(b1.grad)) <= 1e-10 * abs(float(b1.grad))
+        g = grad.contract_with_grad(nw.ising_network(n, e, b), tree, 16)
+        b2 = torch.tensor(b, dtype=torch.float64, requires_grad=True)
+        T2 = ti.ising_tensors(n, e, b2, ones, True)
+        torch.autograd.backward(T2, [torch.from_numpy(x) for x in g.grads])
+        assert abs(float(bb.grad) - float(b2.grad)) < 1e-8 * abs(float(b2.grad))

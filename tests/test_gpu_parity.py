@@ -221,36 +221,6 @@ def test_errors_are_reported(ctx):
         ctx.load_network(broken)
 
 
-def _bond_order_array(t, bonds, order):
-    return np.transpose(t, [bonds.index(b) for b in order])
-
-
-def _pair_product(ta, ba, tb, bb, new_bond):
-    """Contract two tensors over `new_bond`; remaining axes sorted by bond id (gauge-free)."""
-    ia, ib = ba.index(new_bond), bb.index(new_bond)
-    p = np.tensordot(ta, tb, axes=([ia], [ib]))
-    rest = [b for b in ba if b != new_bond] + [b for b in bb if b != new_bond]
-    return _bond_order_array(p, rest, sorted(rest))
-
-
-def _unit(x):
-    return x / np.linalg.norm(x)
-
-
-def _sampled_ops(tree, lx, rows):
-    """(kind, op index, i, j) of the first S and first C op of each given boundary row."""
-    picks = []
-    per_row_c = lx
-    per_row_s = lx - 1
-    for y in rows:
-        base = (y - 1) * (per_row_c + per_row_s)
-        c_idx, s_idx = base + lx // 2, base + per_row_c + per_row_s // 2
-        for idx in (c_idx, s_idx):
-            op = tree.ops[idx]
-            picks.append((op[0], idx, op[1], op[2]))
-    return picks
-
-
 @pytest.fixture(scope="module")
 def full_size(ctx):
     n, edges = nw.square_lattice(32, 32)
@@ -260,36 +230,18 @@ def full_size(ctx):
     return nets, tree, ids
 
 
-def test_full_size_sampled_ops_match_oracle(ctx, full_size):
-    """The benchmark's launch (32x32, D=4, 8 seeds batched, chi=64): sampled ops, one by one.
-
-    For each sampled op, the GPU's input tensors to that op (fetched after the
-    previous op) go through the oracle's step, and the result is compared with
-    the GPU's output: elementwise for a contraction, and the gauge-free product
-    A_bar B_bar for a compression.  Both sides carry power-of-two scales, so
-    results are compared after normalisation.
-    """
+def test_full_size_rows_match_oracle_op_by_op(ctx, full_size):
+    """The benchmark's launch (32x32, D=4, 8 seeds batched, chi=64): every C and S op
+    of boundary rows 6, 18 and 31 (the last absorption row, widest cores) for two
+    instances of the batch, each checked against the oracle's own step on the GPU's
+    inputs (elementwise 1e-12 for contractions, the gauge-free product A_bar B_bar
+    to 1e-10 for compressions)."""
+    from oplevel import row_ops, walk
     nets, tree, ids = full_size
-    for which in (0, 5):
-        for kind, r, i, j in _sampled_ops(tree, 32, (6, 18)):
-            ti, bi = ctx.debug_tensor(ids, which, 64, r - 1, i)
-            tj, bj = ctx.debug_tensor(ids, which, 64, r - 1, j)
-            if kind == "C":
-                k = tree.ops[r][3]
-                tk, bk = ctx.debug_tensor(ids, which, 64, r, k)
-                want, bw = approx.contract_pair(ti, bi, tj, bj)
-                got = _bond_order_array(tk, bk, bw)
-                assert np.linalg.norm(_unit(got) - _unit(want)) < 1e-12
-            else:
-                ai, bai = ctx.debug_tensor(ids, which, 64, r, i)
-                aj, baj = ctx.debug_tensor(ids, which, 64, r, j)
-                new = [b for b in bai if b not in bi][0]
-                res = approx.compress_pair(ti, bi, tj, bj, 64, new)
-                assert res is not None and res[6] > 1e-8
-                want = _pair_product(res[0], res[1], res[2], res[3], new)
-                got = _pair_product(ai, bai, aj, baj, new)
-                assert got.shape == want.shape
-                assert np.linalg.norm(_unit(got) - _unit(want)) < 1e-10
+    ops = [r for y in (6, 18, 31) for r in row_ops(32, y)]
+    res = walk(ctx, ids, tree, 64, ops, (0, 5))
+    print("op-level walk:", res)
+    assert res["c_ops"] == 3 * 32 * 2 and res["ambiguous"] == 0 and res["s_ops"] == 3 * 31 * 2
 
 
 def test_full_size_bit_reproducible_and_in_band(ctx, full_size):
