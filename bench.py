@@ -1,20 +1,35 @@
 """Benchmark: approximate contraction of a frozen tree on GB300 (one JSON line).
 
-Workload (one step = one pass of the whole hot path over one batch): a 32x32
-open square lattice, bond dimension D = 4, entries i.i.d. Normal(0.2, 1),
-8 independent instances (seeds), the boundary-row contraction tree, chi = 64,
-approximately contracted to log|Z| in the FP64 form.  value = log|Z|
-evaluations per second (instances / step time), inputs resident in HBM; e2e =
-the same through the C ABI with the inputs copied from pinned host memory and
-the results read back every step.
+One step = one pass of the whole hot path (schedule expansion cached, every
+contraction, compression, rescale and the final read-out) over one batch of
+instances, inputs resident in HBM.  value = log|Z| evaluations per second
+(instances / step time) on the fastest arithmetic form that meets the metric's
+gate; e2e = the same through the C ABI with the inputs copied from pinned host
+memory and the results read back every step.
+
+Workloads (--workload):
+  normal32  (default) 32x32 open square lattice, D = 4, entries i.i.d.
+            Normal(0.2, 1), 8 independent seeds per GPU, boundary-row tree,
+            chi = 64.  Its truncated result is rounding-chaotic (a 1e-15
+            change of one input moves ln|Z| by ~1e-4 relative), so the gate
+            of each reduced-precision form is judged on a 16x16 calibration
+            batch of the same shapes, where FP64 results are well defined.
+  ising64   64x64 open square lattice Ising model, J = 1, the beta sweep
+            beta_t = 0.2 + 0.5 t / 255; a step is one batch of --batch betas
+            (default 32, every 8th value of the sweep, plus the betas that
+            have stored oracle values), chi = 128.  Each form's error is
+            measured against the stored oracle values; the gate at each beta
+            is max(1e-6, 4 x the oracle's own rounding spread there).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Multi-GPU (torchrun): every rank contracts its own 8 instances (weak scaling,
+                       [--workload normal32|ising64] [--batch B]
+Multi-GPU (torchrun): every rank contracts its own instances (weak scaling,
 no data-path collective); rank 0 prints the line.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -28,39 +43,151 @@ sys.path.insert(0, ROOT)
 
 METRIC = "log Z evals/sec & contraction TFLOP/s vs plain FP64 GPU form at logZ rel err≤1e-6"
 UNIT = "evals/s"
-L, D, CHI, INSTANCES = 32, 4, 64, 8
+GATE = 1e-6
+
+# DRAM bytes (read + write) of one launch of the FP64 polish (block_jacobi_kernel<double>)
+# on 8 cores of 256 x 256, from one Nsight Compute capture; valid only for the kernel
+# source it was taken on (sha256 prefix of csrc/k_svd.cu), else the line reports null.
+JACOBI_TRAFFIC = {"bytes": 4.285952e6, "k_svd_sha": "", "source": "profiles/block_jacobi_kernel_f64_8x8_d4_chi64_batch8.md"}
 
 
-def workload_name():
-    return (f"{L}x{L} open square lattice, D={D}, entries i.i.d. Normal(0.2,1), "
-            f"{INSTANCES} seeds per GPU, boundary-row tree, chi={CHI}")
-
-
-def load_peaks():
+def host_cores() -> int:
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
-    except OSError:
-        return {}
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
-# FP64 ALU peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-
-# DRAM bytes (read + write) of one launch of the FP64 polish on 8 cores of 256 x 256,
-# the shape and batch of the bulk of this workload's launches: dram__bytes_read.sum +
-# dram__bytes_write.sum from one Nsight Compute capture of such a launch; to be
-# retaken whenever that kernel changes.
-JACOBI_F64_DRAM_BYTES_PER_LAUNCH = 4.285952e6
+def source_sha(rel: str) -> str:
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def build_inputs(rank: int, n_inst: int):
-    from tn_inputs import networks as nw
-    from tn_inputs import trees as tr
-    n, edges = nw.square_lattice(L, L)
-    tree = tr.boundary_rows(L, L)
-    nets = [nw.random_network(n, edges, D, seed=rank * n_inst + s) for s in range(n_inst)]
-    return nets, tree
+# ---------------------------------------------------------------------------
+# workloads
+
+
+class Normal32:
+    name = "normal32"
+    L, D, CHI, N = 32, 4, 64, 8
+    CAL_L, CAL_N = 16, 4
+
+    def __init__(self, args):
+        self.N = args.batch or self.N
+
+    def describe(self):
+        return (f"{self.L}x{self.L} open square lattice, D={self.D}, entries i.i.d. Normal(0.2,1), "
+                f"{self.N} seeds per GPU, boundary-row tree, chi={self.CHI}")
+
+    def tree(self):
+        from tn_inputs import trees as tr
+        return tr.boundary_rows(self.L, self.L)
+
+    def nets(self, rank):
+        from tn_inputs import networks as nw
+        n, edges = nw.square_lattice(self.L, self.L)
+        return [nw.random_network(n, edges, self.D, seed=rank * self.N + s) for s in range(self.N)]
+
+    def cpu_net(self, idx):
+        from tn_inputs import networks as nw
+        n, edges = nw.square_lattice(self.L, self.L)
+        return nw.random_network(n, edges, self.D, seed=idx)
+
+    def cpu_rows(self):
+        return 8
+
+    def forms(self, ctx, torch, ids):
+        """Each reduced-precision form on a 16x16 calibration batch (same D, chi, shapes per
+        compression), error relative to the FP64 form there; the FP64 form's own error is 0."""
+        from tn_inputs import networks as nw
+        from tn_inputs import trees as tr
+        n, edges = nw.square_lattice(self.CAL_L, self.CAL_L)
+        tree = tr.boundary_rows(self.CAL_L, self.CAL_L)
+        cal = [ctx.load_tree(ctx.load_network(nw.random_network(n, edges, self.D, seed=1000 + s)), tree)
+               for s in range(self.CAL_N)]
+        out = {"how": f"error on a {self.CAL_L}x{self.CAL_L} calibration batch ({self.CAL_N} seeds, same D and chi) "
+                      f"against the FP64 form; speed on the benchmark batch",
+               "gate_rel_err": GATE}
+        ref = None
+        for prec in ("f64", "tf32x3", "tf32", "bf16"):
+            lz, _ = ctx.contract(cal, self.CHI, prec)
+            if ref is None:
+                ref = lz
+            err = float(max(abs(a - b) / abs(b) for a, b in zip(lz, ref)))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.contract(ids, self.CHI, prec)
+            torch.cuda.synchronize()
+            out[prec] = {"evals_per_s": len(ids) / (time.perf_counter() - t0), "max_rel_err": err,
+                         "meets_gate": bool(err <= GATE)}
+        return out
+
+
+class Ising64:
+    name = "ising64"
+    L, CHI, SWEEP = 64, 128, 256
+
+    def __init__(self, args):
+        self.B = args.batch or 32
+        with open(os.path.join(ROOT, "tests", "golden", "ising64_chi128.json")) as f:
+            self.gold = json.load(f)["entries"]
+
+    def describe(self):
+        return (f"{self.L}x{self.L} open square lattice Ising, J=1, beta sweep 0.2..0.7 ({self.SWEEP} values), "
+                f"batch of {self.B} betas per GPU per step, boundary-row tree, chi={self.CHI}")
+
+    def betas(self, rank):
+        from tn_inputs import networks as nw
+        sweep = nw.beta_sweep(self.SWEEP)
+        ts = [e["t"] for e in self.gold]
+        step = max(1, self.SWEEP // self.B)
+        for t in range(rank % step, self.SWEEP, step):
+            if len(ts) >= self.B:
+                break
+            if t not in ts:
+                ts.append(t)
+        return [float(sweep[t]) for t in ts[:self.B]]
+
+    def tree(self):
+        from tn_inputs import trees as tr
+        return tr.boundary_rows(self.L, self.L)
+
+    def nets(self, rank):
+        from tn_inputs import networks as nw
+        n, edges = nw.square_lattice(self.L, self.L)
+        return [nw.ising_network(n, edges, b) for b in self.betas(rank)]
+
+    def cpu_net(self, idx):
+        from tn_inputs import networks as nw
+        n, edges = nw.square_lattice(self.L, self.L)
+        return nw.ising_network(n, edges, float(nw.beta_sweep(self.SWEEP)[(idx * 37) % self.SWEEP]))
+
+    def cpu_rows(self):
+        return 8
+
+    def forms(self, ctx, torch, ids):
+        """Each form on the benchmark batch itself, error against the stored oracle values."""
+        out = {"how": "error against the stored oracle values at the batch's golden betas; gate at each beta = "
+                      "max(1e-6, 4 x the oracle's rounding spread there)", "gate_rel_err": GATE,
+               "band": {"%.4f" % e["beta"]: max(GATE, 4 * e["spread_rel"]) for e in self.gold}}
+        ng = len(self.gold)
+        for prec in ("f64", "tf32x3", "tf32", "bf16"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lz, _ = ctx.contract(ids, self.CHI, prec)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            errs = [abs(a - e["logabsz"]) / abs(e["logabsz"]) for a, e in zip(lz[:ng], self.gold)]
+            ok = all(x <= max(GATE, 4 * e["spread_rel"]) for x, e in zip(errs, self.gold))
+            out[prec] = {"evals_per_s": len(ids) / dt, "max_rel_err": max(errs), "rel_errs": errs,
+                         "meets_gate": bool(ok)}
+        return out
+
+
+WORKLOADS = {"normal32": Normal32, "ising64": Ising64}
+
+
+# ---------------------------------------------------------------------------
 
 
 class ClockSampler:
@@ -147,7 +274,6 @@ def max_over_ranks(x: float, device) -> float:
 
 
 def barrier(device):
-    import torch
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
         if dist.get_backend() == "nccl":
@@ -161,54 +287,43 @@ def barrier(device):
 
 
 def _oracle_prefix(args):
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    rank_seed, n_ops = args
+    wname, idx, n_ops = args
     sys.path.insert(0, ROOT)
-    from tn_inputs import networks as nw
-    from tn_inputs import trees as tr
     from tn_inputs.formats import Tree
     from oracle import approx
-    n, edges = nw.square_lattice(L, L)
-    net = nw.random_network(n, edges, D, seed=rank_seed)
-    tree = tr.boundary_rows(L, L)
+    wl = WORKLOADS[wname](argparse.Namespace(batch=0))
+    net = wl.cpu_net(idx)
+    tree = wl.tree()
     t0 = time.time()
-    sub = Tree(tree.n_inputs, tree.ops[:n_ops])
-    # run the prefix of the schedule (the remaining tensors are left open)
     try:
-        approx.contract(net, sub, CHI)
+        approx.contract(net, Tree(tree.n_inputs, tree.ops[:n_ops]), wl.CHI)
     except ValueError:
         pass  # the prefix leaves open tensors: expected
     return time.time() - t0
 
 
-def oracle_sample(rows: int = 8, cores: int | None = None):
-    """Time the oracle on the first `rows` boundary rows of the tree, one seed per core.
+def oracle_sample(wl, rows: int = 0, cores: int = 0):
+    """The oracle on the first `rows` boundary rows of the tree, one instance per host core.
 
-    Returns (evals/s extrapolated by traced cost, cores used, description).
+    Returns (evals/s extrapolated by the traced cost, cores used, description).
     """
     import multiprocessing as mp
-    from tn_inputs import networks as nw
     from tn_inputs import trees as tr
     from tn_inputs.formats import Tree
-    n, edges = nw.square_lattice(L, L)
-    tree = tr.boundary_rows(L, L)
-    bonds = nw.random_network(n, edges, D, seed=0)
-    full = tr.trace_cost(bonds.bonds, bonds.bond_dims, tree, CHI)["total"]
-    # a prefix of the schedule (8 rows: about a fifth of the traced cost, ~10 s per core)
-    per_row = 2 * L - 1
-    n_ops = per_row * rows
-    part = tr.trace_cost(bonds.bonds, bonds.bond_dims, Tree(tree.n_inputs, tree.ops[:n_ops]), CHI)["total"]
-    cores = cores or max(1, min(os.cpu_count() or 1, 16))
-    jobs = max(cores, 1)
-    ctx = mp.get_context("spawn")
+    tree = wl.tree()
+    net0 = wl.cpu_net(0)
+    full = tr.trace_cost(net0.bonds, net0.bond_dims, tree, wl.CHI)["total"]
+    rows = rows or wl.cpu_rows()
+    n_ops = (2 * wl.L - 1) * rows
+    part = tr.trace_cost(net0.bonds, net0.bond_dims, Tree(tree.n_inputs, tree.ops[:n_ops]), wl.CHI)["total"]
+    cores = cores or host_cores()
     saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in saved:
         os.environ[k] = "1"   # inherited by the spawned workers: one BLAS thread each
     try:
         t0 = time.time()
-        with ctx.Pool(cores) as pool:
-            times = pool.map(_oracle_prefix, [(s, n_ops) for s in range(jobs)])
+        with mp.get_context("spawn").Pool(cores) as pool:
+            times = pool.map(_oracle_prefix, [(wl.name, s, n_ops) for s in range(cores)])
         wall = time.time() - t0
     finally:
         for k, v in saved.items():
@@ -217,56 +332,31 @@ def oracle_sample(rows: int = 8, cores: int | None = None):
             else:
                 os.environ[k] = v
     frac = part / full
-    evals = jobs * frac / wall
-    desc = (f"oracle on the first {n_ops} tree ops ({100 * frac:.1f}% of the traced cost) of {jobs} seeds, "
-            f"one process per core, OPENBLAS_NUM_THREADS=1; evals/s = seeds x fraction / wall "
-            f"({wall:.1f} s wall, mean {sum(times) / len(times):.1f} s per seed)")
+    evals = cores * frac / wall
+    desc = (f"oracle on the first {n_ops} tree ops ({100 * frac:.1f}% of the traced cost) of {cores} instances, "
+            f"one process per host core ({cores} of {os.cpu_count()}), OPENBLAS_NUM_THREADS=1; evals/s = instances "
+            f"x fraction / wall ({wall:.1f} s wall, mean {sum(times) / len(times):.1f} s per instance)")
     return evals, cores, desc
 
 
-# ---------------------------------------------------------------------------
-# GEMM forms on a smaller calibration batch
-
-CAL_L, CAL_INSTANCES = 16, 4
-
-
-def calibrate_forms(ctx, torch):
-    """Throughput and log|Z| error of each GEMM form against the FP64 form.
-
-    Runs a 16x16 open lattice (D=4, Normal(0.2,1), boundary-row tree, chi=64;
-    the same shapes per compression as the full workload) as one batch per form,
-    and the FP64 form once more with one instance per call.  The error is the
-    largest |ln|Z|_form - ln|Z|_f64| / |ln|Z|_f64| over the batch; a form meets the
-    metric's gate at 1e-6.
-    """
-    from tn_inputs import networks as nw
-    from tn_inputs import trees as tr
-    n, edges = nw.square_lattice(CAL_L, CAL_L)
-    tree = tr.boundary_rows(CAL_L, CAL_L)
-    ids = []
-    for s in range(CAL_INSTANCES):
-        nid = ctx.load_network(nw.random_network(n, edges, D, seed=1000 + s))
-        ids.append(ctx.load_tree(nid, tree))
-    out = {"workload": f"{CAL_L}x{CAL_L} open square lattice, D={D}, Normal(0.2,1), {CAL_INSTANCES} seeds, "
-                       f"boundary-row tree, chi={CHI}", "gate_rel_err": 1e-6}
-    ref = None
-    for prec in ("f64", "tf32x3", "tf32", "bf16"):
-        ctx.contract(ids, CHI, prec)
+def fp64_peak_tflops(torch, device):
+    """FP64 rate measured in this run: a cuBLAS DGEMM 8192^3 (best of 3, CUDA events)."""
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device=device)
+    b = torch.randn(n, n, dtype=torch.float64, device=device)
+    c = a @ b
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        lz, _ = ctx.contract(ids, CHI, prec)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if ref is None:
-            ref = lz
-        err = float(max(abs(a - b) / abs(b) for a, b in zip(lz, ref)))
-        out[prec] = {"evals_per_s": CAL_INSTANCES / dt, "rel_err_vs_f64": err, "meets_gate": bool(err <= 1e-6)}
-    t0 = time.perf_counter()
-    for i in ids:
-        ctx.contract([i], CHI, "f64")
-    torch.cuda.synchronize()
-    out["f64_unbatched"] = {"evals_per_s": CAL_INSTANCES / (time.perf_counter() - t0)}
-    return out
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b, c
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 def run_ours(args):
@@ -279,20 +369,23 @@ def run_ours(args):
     torch.cuda.set_device(device)
     from paper_2206_07044_gb300 import Context, build
     build.build()
+    wl = WORKLOADS[args.workload](args)
     stream = torch.cuda.current_stream(device)
     ctx = Context(local, stream=stream)
-    nets, tree = build_inputs(rank, INSTANCES)
+    nets = wl.nets(rank)
+    tree = wl.tree()
     net_ids = [ctx.load_network(x) for x in nets]
     ids = [ctx.load_tree(nid, tree) for nid in net_ids]
-    stats = ctx.plan_stats(ids[0], CHI, args.prec)
+    nb = len(ids)
+    stats = ctx.plan_stats(ids[0], wl.CHI, args.prec)
     # cpu baseline first (spawned pool, before more GPU work), rank 0 only, N = 1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, desc = oracle_sample()
+        v, cores, desc = oracle_sample(wl)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     def step():
-        return ctx.contract(ids, CHI, args.prec)
+        return ctx.contract(ids, wl.CHI, args.prec)
 
     # warm-up: the first pass runs eagerly, the second captures the schedule as a
     # CUDA graph, later passes replay it
@@ -323,76 +416,95 @@ def run_ours(args):
     prof_ms = p0.elapsed_time(p1)
     fam = ctx.kernel_times()
     ctx.profile(False)
-    value = world * INSTANCES / (ms_max / 1e3)
+    value = world * nb / (ms_max / 1e3)
 
     # end to end: pinned host inputs -> device, contraction, results -> host, every step
     pinned = [[torch.from_numpy(np.ascontiguousarray(d)).pin_memory() for d in x.data] for x in nets]
     h2d = sum(int(t.numel()) * 8 for x in pinned for t in x)
-    d2h = INSTANCES * (8 + 4)
+    d2h = nb * (8 + 4)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     torch.cuda.synchronize()
     barrier(device)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         for nid, x in zip(net_ids, pinned):
             ctx.set_network_data(nid, x)
         lz2, sg2 = step()
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, device)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, device)
 
-    # the plain FP64 form: the same contraction, one instance per call (no batching)
-    plain = None
+    # the plain FP64 form: the same contraction, one instance per call (no batching),
+    # timed over several calls after one untimed call
+    plain = forms = None
     if rank == 0 and not args.no_forms:
-        ctx.contract(ids[:1], CHI, "f64")
+        ctx.contract(ids[:1], wl.CHI, "f64")
         torch.cuda.synchronize()
+        calls = args.plain_calls
         t0 = time.perf_counter()
-        ctx.contract(ids[:1], CHI, "f64")
+        for q in range(calls):
+            ctx.contract(ids[q % nb:q % nb + 1], wl.CHI, "f64")
         torch.cuda.synchronize()
-        plain_s = time.perf_counter() - t0
-        plain = {"value": 1.0 / plain_s, "unit": UNIT, "ms_per_eval": plain_s * 1e3,
+        plain_s = (time.perf_counter() - t0) / calls
+        plain = {"value": 1.0 / plain_s, "unit": UNIT, "ms_per_eval": plain_s * 1e3, "calls": calls,
                  "how": "one instance per tn_contract_approx call, FP64, same workload"}
-    forms = calibrate_forms(ctx, torch) if rank == 0 and not args.no_forms else None
+        forms = wl.forms(ctx, torch, ids)
+    fp64_peak = fp64_peak_tflops(torch, device) if rank == 0 else None
 
     if rank != 0:
         return
     # roofline of the dominant kernel family (device time share inside the timed region)
     fam_sorted = sorted(fam, key=lambda r: -r[2])
-    top = fam_sorted[0]
+    top = [r for r in fam_sorted if not r[0].startswith("sweeps:")][0]
     algo = {"jacobi_f64": stats["svd_flops"], "qr_f64": stats["qr_flops"], "gemm_f64": stats["gemm_flops"]}
     launches_per_step = {name: nl for name, nl, _ in fam}
     name, nl, tot_ms = top
     avg_ms = tot_ms / nl
     roof = None
     if name in algo:
-        flops_launch = algo[name] * INSTANCES / max(launches_per_step[name], 1)
+        flops_launch = algo[name] * nb / max(launches_per_step[name], 1)
         achieved = flops_launch / (avg_ms * 1e-3) / 1e12
-        traffic = JACOBI_F64_DRAM_BYTES_PER_LAUNCH if (name == "jacobi_f64" and INSTANCES == 8) else None
-        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_note": "DRAM bytes of one 8 x (256 x 256) launch from ncu; the algorithmic "
-                                "read of those cores is 4.19 MB" if traffic else None,
-                "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (unit counts and clock)",
+        traffic, tsrc = None, None
+        if (name == "jacobi_f64" and wl.name == "normal32" and nb == 8 and
+                JACOBI_TRAFFIC["k_svd_sha"] == source_sha("paper_2206_07044_gb300/csrc/k_svd.cu")):
+            traffic, tsrc = JACOBI_TRAFFIC["bytes"], JACOBI_TRAFFIC["source"]
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": traffic, "traffic_source": tsrc,
+                "peak_source": "FP64 rate measured in this run (cuBLAS DGEMM 8192^3, best of 3)",
+                "peak_unit_counts": 152 * 2 * 2 * 2.07e9 / 1e12,
+                "work": "algorithmic FLOPs of the paper's counts (SVD 4mn^2-4/3n^3, QR 2mn^2-2/3n^3, GEMM 2mnk) "
+                        "over the family's launches",
                 "share_of_step": tot_ms / prof_ms,
                 "timing": "CUDA events around each launch of one profiled pass (eager, one stream)"}
-    gflop_step = (stats["gemm_flops"] + stats["qr_flops"] + stats["svd_flops"]) * INSTANCES * world / 1e9
+    gflop_step = (stats["gemm_flops"] + stats["qr_flops"] + stats["svd_flops"]) * nb * world / 1e9
+    gated = None
+    if forms:
+        ok = [p for p in ("f64", "tf32x3", "tf32", "bf16") if forms.get(p, {}).get("meets_gate")]
+        speed = {p: forms[p].get("evals_per_s", value if p == args.prec else None) for p in ok}
+        speed = {p: v for p, v in speed.items() if v}
+        if speed:
+            best = max(speed, key=speed.get)
+            gated = {"form": best, "evals_per_s": speed[best],
+                     "vs_plain_fp64_unbatched": speed[best] / plain["value"] if plain else None}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.prec == "f64" else args.prec, "data": "synthetic",
-        "config": {"workload": workload_name(), "instances_per_gpu": INSTANCES, "chi": CHI, "prec": args.prec,
-                   "tree": "boundary rows", "l2": "working set %.0f MB per GPU > 129 MB L2 (no flush needed)"
-                   % (stats["peak_bytes"] * INSTANCES / 1e6)},
+        "config": {"workload": wl.describe(), "instances_per_gpu": nb, "chi": wl.CHI, "prec": args.prec,
+                   "tree": "boundary rows",
+                   "l2": "working set %.0f MB per GPU > 129 MB L2 (no flush needed)" % (stats["peak_bytes"] * nb / 1e6)},
         "contraction_tflops": gflop_step / (ms_max / 1e3) / 1e3,
-        "e2e": {"value": world * INSTANCES / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": {"value": world * nb / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "gpu_launches": int(stats["kernel_launches"]) * args.steps,
         "plain_fp64_unbatched": plain,
         "vs_plain_fp64_unbatched": (value / world) / plain["value"] if plain else None,
+        "metric_gate": gated,
         "forms": forms,
         "roofline": roof,
         "kernel_share": {n_: round(t_ / prof_ms, 4) for n_, _, t_ in fam_sorted if not n_.startswith("sweeps:")},
         "jacobi_sweeps_per_matrix": {
             prec_: round(dict((a, b) for a, b, _ in fam).get("sweeps:jacobi_" + prec_, 0) /
-                         max(1, dict((a, b) for a, b, _ in fam).get("jacobi_" + prec_, 0) * INSTANCES), 3)
+                         max(1, dict((a, b) for a, b, _ in fam).get("jacobi_" + prec_, 0) * nb), 3)
             for prec_ in ("f32", "f64")},
         "profiled_pass_ms": prof_ms,
         "graph": graph,
@@ -431,7 +543,6 @@ def run_gemm_check(args):
     flop = 2.0 * E * E * E
     out = {"mode": "gemm_check", "gemm": f"{E} x {E} x {E} (2 g^6 = {flop:.3e} FLOP)", "forms": {}}
     ref = None
-    peaks = load_peaks()
     for prec in ("f64", "tf32", "bf16", "tf32x3"):
         ctx.contract([iid], 1, prec)
         ctx.profile(True)
@@ -445,7 +556,6 @@ def run_gemm_check(args):
             ref = float(lz[0])
         out["forms"][prec] = {"kernel_ms": ms, "tflops": flop / (ms * 1e-3) / 1e12 if ms else None,
                               "rel_logz_vs_f64": abs(float(lz[0]) - ref) / abs(ref)}
-    out["measured_peaks"] = {k: peaks[k] for k in peaks if "tflops" in k} if isinstance(peaks, dict) else None
     ctx.close()
     print(json.dumps(out))
 
@@ -454,20 +564,21 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # each step: a bounded oracle sample of the workload on the host cores
+    wl = WORKLOADS[args.workload](args)
+    # each step: a bounded oracle sample of the workload on all host cores
     for _ in range(args.warmup):
-        oracle_sample(rows=1)
+        oracle_sample(wl, rows=1)
     vals = []
     desc = cores = None
     t0 = time.time()
     for _ in range(args.steps):
-        v, cores, desc = oracle_sample()
+        v, cores, desc = oracle_sample(wl)
         vals.append(v)
     value = sorted(vals)[len(vals) // 2]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": (time.time() - t0) * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(), "instances_per_gpu": INSTANCES, "chi": CHI},
+            "data": "synthetic", "config": {"workload": wl.describe(), "chi": wl.CHI},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -479,16 +590,16 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="normal32", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="instances per GPU per step (0: the workload's default)")
     ap.add_argument("--prec", default="f64", choices=["f64", "tf32", "bf16", "tf32x3"])
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end leg (at most --steps)")
+    ap.add_argument("--plain-calls", type=int, default=3, help="timed calls of the unbatched FP64 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the unbatched and mixed-form legs")
     ap.add_argument("--gemm-check", type=int, default=0, metavar="G",
                     help="instead of the benchmark: throughput of each GEMM form on a (G^2)^3 contraction")
-    ap.add_argument("--L", type=int, default=L, help="lattice side (a smaller case for profiling)")
-    ap.add_argument("--instances", type=int, default=INSTANCES, help="instances per GPU")
     args = ap.parse_args()
-    globals()["L"] = args.L
-    globals()["INSTANCES"] = args.instances
     if args.gemm_check:
         run_gemm_check(args)
     elif args.impl == "reference":

@@ -125,7 +125,12 @@ typedef struct {
  *                      budget had run out: each such GEMM drains its copies
  *                      in flight, releases its TMEM and flags the call,
  *                      which returns TN_ETIMEOUT.  For tests of the bounded
- *                      waits; leave 0 otherwise. */
+ *                      waits; leave 0 otherwise.
+ *   tuner_cache        path of the autotuner's cache file (NULL: none).  On
+ *                      tn_create its choices are loaded if the file exists
+ *                      and was written on the same GPU model (a file from
+ *                      another model is ignored; an unreadable one gives
+ *                      TN_EFORMAT); tn_autotune rewrites it. */
 typedef struct {
   int32_t struct_size;
   int32_t graph_mode;
@@ -134,6 +139,7 @@ typedef struct {
   double tape_budget_bytes;
   int32_t debug_tc_give_up;
   int32_t reserved;
+  const char* tuner_cache;
 } tn_options;
 
 /* Default options (struct_size = sizeof(tn_options)). */
@@ -144,6 +150,28 @@ void tn_options_default(tn_options* opt);
  * struct_size smaller than this version's, fields out of range), TN_ECUDA
  * (no such device). */
 int tn_create(tn_ctx** out, int device, const tn_options* opt);
+
+/* Autotuner of the launch shapes (the survey's tile autotuner): for the plan
+ * of the instances' groups at this chi and form, every distinct launch shape
+ * of the QR, the FP32 and FP64 Jacobi passes (cluster size P of the
+ * one-matrix-per-cluster kernels) and the GEMMs that carry 98% of the plan's
+ * GEMM flops (FP64 tile variant; tensor-core N tile) is timed with each
+ * candidate on random scratch data of that shape and the plan's batch size
+ * (CUDA events, fastest of two launches; the Jacobi passes capped at two
+ * sweeps), and the fastest is recorded in the device's table, which the
+ * launchers consult before their built-in rules.  Results of later calls may
+ * differ in rounding from untuned ones (a different cluster size changes the
+ * order of reductions).  Writes the table to options.tuner_cache when set.
+ * *n_tuned (may be NULL) receives the number of shapes tuned.  Allocates its
+ * own scratch and frees it.  Errors: TN_EINVAL, TN_ENOMEM, TN_ECUDA. */
+int tn_autotune(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, int prec, int* n_tuned);
+
+/* The device's tuned choices as rows of 6 int32 (kernel family, m, n, k,
+ * batch, choice): families 1 QR cluster size, 2 FP64 Jacobi cluster size,
+ * 3 FP32 Jacobi cluster size, 4 FP64 GEMM tile variant (1 64x64, 2 32x32,
+ * 3 128x32, 4 128x16), 5 tensor-core N tile.  Copies up to `cap` rows and
+ * returns the number of entries (rows may be NULL when cap is 0). */
+int tn_tuned_choices(tn_ctx* ctx, int cap, int32_t* rows);
 
 /* Destroy a context and free its device memory.  NULL is ignored. */
 void tn_destroy(tn_ctx* ctx);

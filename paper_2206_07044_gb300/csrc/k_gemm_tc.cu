@@ -34,6 +34,7 @@
 
 #include "tn_cluster.h"
 #include "tn_kernels.h"
+#include "tn_tune.h"
 
 namespace tnk {
 namespace {
@@ -353,8 +354,8 @@ int pick_bn(int n, int mode) {
 
 size_t gemm_tc_workspace_bytes(int m, int n, int k, int mode, int batch) {
   const int eb = mode == 1 ? 2 : 4, bk = 128 / eb, split = mode == 2 ? 2 : 1;
-  const int bn = pick_bn(n, mode);
-  const int64_t mp = (int64_t)(m + kBM - 1) / kBM * kBM, np = (int64_t)(n + bn - 1) / bn * bn;
+  // B^T padded to a multiple of the largest N tile, so any tile choice fits
+  const int64_t mp = (int64_t)(m + kBM - 1) / kBM * kBM, np = (int64_t)(n + 255) / 256 * 256;
   const int64_t kp = (int64_t)((k > 0 ? k : 1) + bk - 1) / bk * bk;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
   return (size_t)(up(mp * kp * eb * batch * split) + up(np * kp * eb * batch * split) + 256);
@@ -368,7 +369,9 @@ cudaError_t gemm_tc(int m, int n, int k, double alpha, View A, View B, ViewW C, 
   if (batch > 65535 || ws_bytes < gemm_tc_workspace_bytes(m, n, k, mode, batch)) return cudaErrorInvalidValue;
   const bool bf16 = mode == 1;
   const int eb = bf16 ? 2 : 4, bk = 128 / eb, split = mode == 2 ? 2 : 1;
-  const int bn = pick_bn(n, mode);
+  // a measured N tile (tn_autotune) first; split TF32 has no 256-wide variant
+  int bn = tune_get(TK_GEMMTC, m, n, k, batch);
+  if (!(bn == 64 || bn == 128 || (bn == 256 && mode != 2))) bn = pick_bn(n, mode);
   const int64_t mp = (int64_t)(m + kBM - 1) / kBM * kBM, np = (int64_t)(n + bn - 1) / bn * bn;
   const int64_t kp = (int64_t)((k > 0 ? k : 1) + bk - 1) / bk * bk;
   if (mp * batch * split > INT32_MAX || np * batch * split > INT32_MAX) return cudaErrorInvalidValue;

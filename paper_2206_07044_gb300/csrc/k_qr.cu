@@ -16,6 +16,7 @@
 
 #include "tn_cluster.h"
 #include "tn_kernels.h"
+#include "tn_tune.h"
 
 namespace cg = cooperative_groups;
 
@@ -265,11 +266,17 @@ cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW 
     const size_t b = ((size_t)nc * m + (size_t)m) * sizeof(double);
     return b <= kQrSmemCap ? b : (size_t)-1;
   };
+  const size_t gsm = (m <= kVSmem) ? (size_t)m * sizeof(double) : 0;
+  // a measured choice (tn_autotune) first
+  const int tp = tune_get(TK_QR, m, n, 0, batch);
+  if (tp >= 1 && tp <= 16) {
+    if (smem_cols(tp) != (size_t)-1) return launch_qr<true>(tp, m, n, A, work, work_bs, taus, R, batch, s, smem_cols(tp));
+    return launch_qr<false>(tp, m, n, A, work, work_bs, taus, R, batch, s, gsm);
+  }
   auto even = [](int) { return 1.0; };
   int P = choose_cluster((const void*)qr_cluster_kernel<true>, kThreads, batch, pmin, pmax, smem_cols, even);
   if (P > 0) return launch_qr<true>(P, m, n, A, work, work_bs, taus, R, batch, s, smem_cols(P));
   // columns do not fit in shared memory: update them in global memory
-  const size_t gsm = (m <= kVSmem) ? (size_t)m * sizeof(double) : 0;
   P = choose_cluster((const void*)qr_cluster_kernel<false>, kThreads, batch, pmin, pmax, [&](int) { return gsm; },
                      even);
   if (P < 1) P = pmax < 8 ? pmax : 8;

@@ -38,6 +38,7 @@
 
 #include "tn_cluster.h"
 #include "tn_kernels.h"
+#include "tn_tune.h"
 
 namespace cg = cooperative_groups;
 
@@ -84,6 +85,7 @@ struct JacArgs {
   T floor_rel;      // columns with |g| <= floor_rel * |G|_F are left alone
   T floor2;         // (set in the kernel) floor_rel^2 * |G|_F^2
   T tol2, sig_tol2; // (set in the kernel) tol^2, sig_tol^2
+  T noise2;         // (set in the kernel) (64 eps |G|_F)^2: the matrix's rounding floor for an off-diagonal
   unsigned long long* sweep_ctr;  // optional: total sweeps run, summed over matrices
   const int* active;  // optional, n ints per matrix (stride act_bs): a pair of two inactive columns is skipped
   int64_t act_bs;
@@ -119,6 +121,11 @@ __device__ T cluster_fro2(cg::cluster_group& cl, const T* G, int m, int n, int r
   double tot = 0.0;
   for (int r = 0; r < P; ++r) tot += __ldcg(slots + r);
   return (T)tot;
+}
+
+template <typename T>
+__device__ __forceinline__ T ab_max(T a, T b) {
+  return a > b ? a : b;
 }
 
 template <typename T, bool kGlobal>
@@ -175,10 +182,17 @@ __device__ __forceinline__ bool jacobi_pair(T* gx, T* gy, T* vx, T* vy, int m, i
   const T t = (d >= T(0) ? h : -h) / (fabs(d) + sqrt(d * d + h * h));
   const T c = rsqrt(T(1) + t * t);
   const T s = c * t;
+  const T mx = ab_max(al, be);
   __syncwarp();
   rot_cols_norms<T, kGlobal>(gx, gy, m, c, s, lane, al, be);
   if (vx) rot_cols_g<T, kGlobal>(vx, vy, n, c, s, lane);
-  return g2 > p.sig_tol2 * ab;
+  // Not yet converged: the relative off-diagonal exceeds sig_tol, and the
+  // off-diagonal itself is above the rounding floor of the matrix.  A column
+  // of norm |y| << |G|_F receives rounding of order eps |G|_F from every
+  // rotation against a large column, so its relative off-diagonals stall near
+  // eps |G|_F / |y|; such a pair can only turn the large column by ~eps and is
+  // counted as converged.
+  return g2 > p.sig_tol2 * ab && g2 > p.noise2 * mx;
 }
 
 template <typename T>
@@ -195,7 +209,12 @@ __global__ void __launch_bounds__(kMaxJacThreads) block_jacobi_kernel(JacArgs<T>
   const bool has_v = (p.V != nullptr);  // without V only G is rotated
   T* V = has_v ? p.V + (int64_t)bidx * p.v_bs : nullptr;
   int* cnt = p.ws + kWsInts * bidx;
-  p.floor2 = p.floor_rel * p.floor_rel * cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
+  {
+    const T fro2 = cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
+    const T eps64 = T(64) * (sizeof(T) == sizeof(double) ? T(DBL_EPSILON) : T(FLT_EPSILON));
+    p.floor2 = p.floor_rel * p.floor_rel * fro2;
+    p.noise2 = eps64 * eps64 * fro2;
+  }
   p.tol2 = p.tol * p.tol;
   p.sig_tol2 = p.sig_tol * p.sig_tol;
 
@@ -338,7 +357,12 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
   T* G = p.G + (int64_t)bidx * p.g_bs;
   T* V = p.V ? p.V + (int64_t)bidx * p.v_bs : nullptr;
   int* cnt = p.ws + kWsInts * bidx;
-  p.floor2 = p.floor_rel * p.floor_rel * cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
+  {
+    const T fro2 = cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
+    const T eps64 = T(64) * (sizeof(T) == sizeof(double) ? T(DBL_EPSILON) : T(FLT_EPSILON));
+    p.floor2 = p.floor_rel * p.floor_rel * fro2;
+    p.noise2 = eps64 * eps64 * fro2;
+  }
   p.tol2 = p.tol * p.tol;
   p.sig_tol2 = p.sig_tol * p.sig_tol;
   const int np = n + (n & 1);
@@ -448,8 +472,12 @@ cudaError_t launch_jacobi(const JacArgs<T>& a, int batch, cudaStream_t s) {
   // The FP64 polish is bound by the SM's FP64 pipe, so a wave counts clusters
   // whose CTAs each own an SM; the FP32 pass is latency-bound and shares SMs well.
   const bool fp64 = sizeof(T) == sizeof(double);
-  int P = choose_cluster((const void*)block_jacobi_kernel<T>, batch, pmax / 2 > 0 ? pmax / 2 : 1, pmax, smem_of,
-                         imbalance, threads_of, fp64);
+  // a measured choice (tn_autotune) first, else the residency rule
+  const int tp = tune_get(fp64 ? TK_JAC64 : TK_JAC32, a.m, a.n, 0, batch);
+  int P = (tp >= 1 && tp <= 16 && smem_of(tp) != (size_t)-1)
+              ? tp
+              : choose_cluster((const void*)block_jacobi_kernel<T>, batch, pmax / 2 > 0 ? pmax / 2 : 1, pmax, smem_of,
+                               imbalance, threads_of, fp64);
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(P > 0 ? threads_of(P) : kThreads, 1, 1);
   cfg.stream = s;
@@ -611,10 +639,10 @@ int grid1d(int64_t n) {
 }  // namespace
 
 cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64_t v_bs, int* ws,
-                           DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr) {
+                           DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr, int max_sweeps) {
   // a preconditioner: running out of sweeps is not an error (the FP64 stage decides)
-  JacArgs<float> a{m, n, G, g_bs, V, v_bs, nullptr, 0, ws, nullptr, 1, 60,
-                   4.0f * (float)m * FLT_EPSILON, 3e-4f, 1e-6f, 0.0f, 0.0f, 0.0f, sweep_ctr, nullptr, 0};
+  JacArgs<float> a{m, n, G, g_bs, V, v_bs, nullptr, 0, ws, nullptr, 1, max_sweeps > 0 ? max_sweeps : 60,
+                   4.0f * (float)m * FLT_EPSILON, 3e-4f, 1e-6f, 0.0f, 0.0f, 0.0f, 0.0f, sweep_ctr, nullptr, 0};
   return launch_jacobi(a, batch, s);
 }
 
@@ -627,7 +655,7 @@ cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int
   // never keep the sweep loop alive
   const double rt = sqrt((double)(m > 16 ? m : 16));
   JacArgs<double> a{m, n, G, g_bs, V, v_bs, sig, sig_bs, ws, st.status, init_v, max_sweeps > 0 ? max_sweeps : 60,
-                    rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, 0.0, 0.0, sweep_ctr, active, act_bs};
+                    rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, 0.0, 0.0, 0.0, sweep_ctr, active, act_bs};
   return launch_jacobi(a, batch, s);
 }
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <fstream>
 #include <map>
 #include <memory>
@@ -18,6 +19,7 @@
 #include "tn_exec.h"
 #include "tn_kernels.h"
 #include "tn_plan.h"
+#include "tn_tune.h"
 
 namespace {
 
@@ -117,6 +119,7 @@ struct tn_ctx {
   double tape_budget = 0.0;  // tn_grad: tape bytes before checkpointing (0: half the free device memory)
   int opt_max_sweeps = 0;    // > 0: FP64 Jacobi sweep cap (tests of the bounded loop)
   bool opt_tc_give_up = false;  // tests: tensor-core GEMM pipeline waits give up at once
+  std::string tuner_cache;      // autotuner cache file ("" = none)
   uint64_t plan_serial = 0;
   uint64_t buf_gen = 0;  // bumped whenever a buffer a captured graph points into moves
   cudaStream_t cap = nullptr;
@@ -545,6 +548,57 @@ bool read_file(const char* path, std::string* out) {
 
 }  // namespace
 
+namespace {
+
+// Time `launch` (one launch per call) on stream s: one untimed launch, then the
+// fastest of two timed ones (ms); a negative value if a launch failed.
+template <typename F>
+double time_launch(cudaStream_t s, F launch) {
+  if (launch() != cudaSuccess) {
+    cudaGetLastError();
+    return -1.0;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = -1.0;
+  for (int r = 0; r < 2; ++r) {
+    cudaEventRecord(e0, s);
+    const cudaError_t e = launch();
+    cudaEventRecord(e1, s);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      best = -1.0;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0 || ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+void fill_random(std::vector<double>& h, uint64_t seed) {
+  uint64_t x = seed * 0x9E3779B97F4A7C15ull + 1;
+  for (double& v : h) {
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    v = (double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+}
+
+struct TuneKey {
+  int kernel, m, n, k;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kernel, m, n, k) < std::tie(o.kernel, o.m, o.n, o.k);
+  }
+};
+
+}  // namespace
+
 extern "C" {
 
 const char* tn_version(void) { return "tn-gb300 0.1"; }
@@ -578,6 +632,15 @@ int tn_create(tn_ctx** out, int device, const tn_options* opt) {
   c->tape_budget = o.tape_budget_bytes;
   c->opt_max_sweeps = o.debug_max_sweeps;
   c->opt_tc_give_up = o.debug_tc_give_up != 0;
+  if (o.tuner_cache && *o.tuner_cache) {
+    c->tuner_cache = o.tuner_cache;
+    DeviceGuard g(device);
+    const std::string e = tnk::tune_load(c->tuner_cache);
+    if (!e.empty()) {
+      delete c;
+      return TN_EFORMAT;
+    }
+  }
   *out = c;
   return TN_OK;
 }
@@ -964,6 +1027,172 @@ int tn_debug_tensor(tn_ctx* c, int n_inst, const int* inst_ids, int which, int c
   cudaError_t e = cudaMemcpy(out, base + (int64_t)which * rec->view.bs, sizeof(double) * size, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "fetch tensor");
   return TN_OK;
+}
+
+int tn_autotune(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, int* n_tuned) {
+  if (!c || !inst_ids || n_inst < 1) return fail(c, TN_EINVAL, "bad arguments");
+  if (chi < 1) return fail(c, TN_EINVAL, "chi must be >= 1");
+  if (prec < TN_F64 || prec > TN_TF32X3) return fail(c, TN_EINVAL, "unknown precision form");
+  for (int q = 0; q < n_inst; ++q)
+    if (inst_ids[q] < 0 || inst_ids[q] >= (int)c->insts.size()) return fail(c, TN_EINVAL, "unknown instance id");
+  DeviceGuard g(c->device);
+  c->dbg_stop = -2;
+  int tuned = 0;
+  std::vector<bool> done(n_inst, false);
+  for (int q = 0; q < n_inst; ++q) {
+    if (done[q]) continue;
+    int batch = 0;
+    for (int r = q; r < n_inst; ++r)
+      if (!done[r] && same_group(c, inst_ids[q], inst_ids[r])) {
+        done[r] = true;
+        ++batch;
+      }
+    int rc = TN_OK;
+    const tnp::Plan* plan = get_plan(c, inst_ids[q], chi, prec, &rc);
+    if (!plan) return rc;
+    // distinct launch shapes; GEMMs by their share of the plan's GEMM flops
+    std::map<TuneKey, double> work;
+    std::map<TuneKey, bool> with_v;
+    for (const tnp::Step& st : plan->steps) {
+      if (st.kind == tnp::ST_QR) work[{tnk::TK_QR, st.m, st.n, 0}] += 1.0;
+      if (st.kind == tnp::ST_JACOBI) {
+        work[{tnk::TK_JAC64, st.m, st.n, 0}] += 1.0;
+        with_v[{tnk::TK_JAC64, st.m, st.n, 0}] = !st.no_v;
+      }
+      if (st.kind == tnp::ST_JACOBI32) work[{tnk::TK_JAC32, st.m, st.n, 0}] += 1.0;
+      if (st.kind == tnp::ST_GEMM) work[{tnk::TK_GEMM64, st.m, st.n, st.k}] += 2.0 * st.m * st.n * (double)st.k;
+      if (st.kind == tnp::ST_GEMM_TC) work[{tnk::TK_GEMMTC, st.m, st.n, st.k}] += 2.0 * st.m * st.n * (double)st.k;
+    }
+    std::vector<std::pair<double, TuneKey>> gemms;
+    double gemm_total = 0.0;
+    for (const auto& w : work)
+      if (w.first.kernel == tnk::TK_GEMM64 || w.first.kernel == tnk::TK_GEMMTC) {
+        gemms.push_back({w.second, w.first});
+        gemm_total += w.second;
+      }
+    std::sort(gemms.begin(), gemms.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<TuneKey> keys;
+    for (const auto& w : work)
+      if (w.first.kernel != tnk::TK_GEMM64 && w.first.kernel != tnk::TK_GEMMTC) keys.push_back(w.first);
+    double covered = 0.0;
+    for (const auto& gk : gemms) {  // the GEMM shapes that carry 98% of the GEMM flops, at most 24
+      if (covered >= 0.98 * gemm_total || (int)keys.size() >= 64) break;
+      keys.push_back(gk.second);
+      covered += gk.first;
+    }
+    cudaStream_t s = c->stream;
+    for (const TuneKey& key : keys) {
+      const int m = key.m, n = key.n, k = key.k;
+      // scratch operands of one launch of this shape (random entries)
+      size_t elems = 0, aux = 0;
+      if (key.kernel == tnk::TK_QR) elems = (size_t)m * n, aux = (size_t)m * n + n + (size_t)std::min(m, n) * n;
+      if (key.kernel == tnk::TK_JAC64 || key.kernel == tnk::TK_JAC32)
+        elems = (size_t)m * n, aux = (size_t)n * n + n;
+      if (key.kernel == tnk::TK_GEMM64 || key.kernel == tnk::TK_GEMMTC)
+        elems = (size_t)m * k + (size_t)k * n, aux = (size_t)m * n;
+      double* d_in = nullptr;
+      double* d_aux = nullptr;
+      void* d_ws = nullptr;
+      size_t ws_bytes = 0;
+      if (key.kernel == tnk::TK_GEMMTC) ws_bytes = tnk::gemm_tc_workspace_bytes(m, n, k, prec == 1 ? 0 : (prec == 2 ? 1 : 2), batch);
+      if (cudaMalloc(&d_in, sizeof(double) * elems * batch) != cudaSuccess ||
+          cudaMalloc(&d_aux, sizeof(double) * aux * batch) != cudaSuccess ||
+          (ws_bytes && cudaMalloc(&d_ws, ws_bytes) != cudaSuccess)) {
+        cudaFree(d_in);
+        cudaFree(d_aux);
+        cudaFree(d_ws);
+        cudaGetLastError();
+        return fail(c, TN_ENOMEM, "autotune scratch allocation failed");
+      }
+      {
+        std::vector<double> h(elems * batch);
+        fill_random(h, (uint64_t)(m * 131 + n * 7 + k));
+        if (key.kernel == tnk::TK_JAC32) {  // the FP32 pass reads floats
+          std::vector<float> hf(h.begin(), h.end());
+          cudaMemcpy(d_in, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice);
+        } else {
+          cudaMemcpy(d_in, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice);
+        }
+      }
+      const void* old_scratch = c->expo;
+      rc = ensure_scratch(c, batch);
+      if (rc != TN_OK) return rc;
+      if (old_scratch != c->expo) drop_graphs(c);  // captured graphs point at the old scratch
+      if (!c->tc_err && cudaMalloc(&c->tc_err, sizeof(int)) != cudaSuccess) return fail(c, TN_ENOMEM, "error word");
+      tnk::DevState ds{c->expo, c->status};
+      std::vector<int> cands;
+      if (key.kernel == tnk::TK_QR || key.kernel == tnk::TK_JAC64 || key.kernel == tnk::TK_JAC32) {
+        for (int P : {1, 2, 3, 4, 6, 8, 10, 12, 14, 16})
+          if (P * 8 <= std::max(8, n)) cands.push_back(P);
+      } else if (key.kernel == tnk::TK_GEMM64) {
+        cands = {1, 2, 3, 4};
+      } else {
+        cands = {64, 128};
+        if (prec != TN_TF32X3) cands.push_back(256);
+      }
+      const int saved = tnk::tune_get(key.kernel, m, n, k, batch);
+      int best = 0;
+      double best_ms = -1.0;
+      for (int cand : cands) {
+        tnk::tune_set(key.kernel, m, n, k, batch, cand);
+        auto launch = [&]() -> cudaError_t {
+          switch (key.kernel) {
+            case tnk::TK_QR:
+              return tnk::qr_r_f64(m, n, tnk::View{d_in, 1, m, (int64_t)m * n}, d_aux, (int64_t)m * n,
+                                   tnk::ViewW{d_aux + ((size_t)m * n + n) * batch, n, 1, (int64_t)std::min(m, n) * n},
+                                   batch, s);
+            case tnk::TK_JAC64:
+              return tnk::jacobi_svd_f64(m, n, d_in, (int64_t)m * n, with_v[key] ? d_aux : nullptr, (int64_t)n * n,
+                                         d_aux + (size_t)n * n * batch, n, c->jac_ws, ds, 1, batch, s, nullptr,
+                                         1e-300, 2);
+            case tnk::TK_JAC32:
+              return tnk::jacobi_svd_f32(m, n, reinterpret_cast<float*>(d_in), (int64_t)m * n,
+                                         reinterpret_cast<float*>(d_aux), (int64_t)n * n, c->jac_ws, ds, batch, s,
+                                         nullptr, 2);
+            case tnk::TK_GEMM64:
+              return tnk::gemm_f64(m, n, k, 1.0, tnk::View{d_in, k, 1, (int64_t)m * k},
+                                   tnk::View{d_in + (size_t)m * k * batch, n, 1, (int64_t)k * n}, 0.0,
+                                   tnk::ViewW{d_aux, n, 1, (int64_t)m * n}, batch, s);
+            default:
+              return tnk::gemm_tc(m, n, k, 1.0, tnk::View{d_in, k, 1, (int64_t)m * k},
+                                  tnk::View{d_in + (size_t)m * k * batch, n, 1, (int64_t)k * n},
+                                  tnk::ViewW{d_aux, n, 1, (int64_t)m * n}, batch,
+                                  prec == 1 ? 0 : (prec == 2 ? 1 : 2), d_ws, ws_bytes, c->tc_err, s);
+          }
+        };
+        const double ms = time_launch(s, launch);
+        if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
+          best_ms = ms;
+          best = cand;
+        }
+      }
+      tnk::tune_set(key.kernel, m, n, k, batch, best > 0 ? best : saved);
+      if (best > 0) ++tuned;
+      cudaFree(d_in);
+      cudaFree(d_aux);
+      cudaFree(d_ws);
+      // the scratch runs may have flagged statuses (capped sweeps): clear them
+      cudaMemsetAsync(c->status, 0, sizeof(int) * batch, s);
+      cudaMemsetAsync(c->tc_err, 0, sizeof(int), s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "autotune");
+    }
+  }
+  if (n_tuned) *n_tuned = tuned;
+  drop_graphs(c);  // recapture with the tuned launch shapes
+  if (!c->tuner_cache.empty()) {
+    const std::string e = tnk::tune_save(c->tuner_cache);
+    if (!e.empty()) return fail(c, TN_EINVAL, "tuner cache: " + e);
+  }
+  return TN_OK;
+}
+
+int tn_tuned_choices(tn_ctx* c, int cap, int32_t* rows) {
+  if (!c || cap < 0 || (cap > 0 && !rows)) return fail(c, TN_EINVAL, "bad arguments");
+  DeviceGuard g(c->device);
+  const auto e = tnk::tune_entries();
+  for (int i = 0; i < cap && i < (int)e.size(); ++i)
+    for (int j = 0; j < 6; ++j) rows[6 * i + j] = e[i][j];
+  return (int)e.size();
 }
 
 int tn_plan_stats_get(tn_ctx* c, int inst_id, int chi, int prec, tn_plan_stats* out) {

@@ -61,7 +61,8 @@ cudaError_t mark_active_f64(int m, int n, int k, const double* G, int64_t g_bs, 
                             cudaStream_t s);
 // The FP32 preconditioning pass (V = I first); never sets a status.
 cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64_t v_bs, int* ws,
-                           DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr);
+                           DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr,
+                           int max_sweeps = 0);
 // y = (float) x and y1 (= y2 when given) = (double) x, n elements per batch.
 cudaError_t convert_f64_to_f32(const double* x, int64_t n, int64_t xbs, float* y, int64_t ybs,
                                int batch, cudaStream_t s);

@@ -49,7 +49,7 @@ class PlanStats(C.Structure):
 class Options(C.Structure):
     _fields_ = [("struct_size", C.c_int32), ("graph_mode", C.c_int32), ("grad_segments", C.c_int32),
                 ("debug_max_sweeps", C.c_int32), ("tape_budget_bytes", C.c_double),
-                ("debug_tc_give_up", C.c_int32), ("reserved", C.c_int32)]
+                ("debug_tc_give_up", C.c_int32), ("reserved", C.c_int32), ("tuner_cache", C.c_char_p)]
 
 
 # every symbol include/tn.h declares, with its ctypes signature
@@ -57,6 +57,8 @@ SIGNATURES = {
     "tn_version": (C.c_char_p, []),
     "tn_options_default": (None, [C.POINTER(Options)]),
     "tn_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(Options)]),
+    "tn_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "tn_tuned_choices": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int32)]),
     "tn_destroy": (None, [C.c_void_p]),
     "tn_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tn_set_graph_mode": (C.c_int, [C.c_void_p, C.c_int]),
@@ -153,14 +155,17 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None, **options):
         """options: any field of tn_options (graph_mode, grad_segments,
-        tape_budget_bytes, debug_max_sweeps, debug_tc_give_up); the rest keep
-        their defaults."""
+        tape_budget_bytes, debug_max_sweeps, debug_tc_give_up, tuner_cache);
+        the rest keep their defaults."""
         self._L = lib()
         opt = Options()
         self._L.tn_options_default(C.byref(opt))
         for k, v in options.items():
             if k in ("struct_size", "reserved") or k not in dict(Options._fields_):
                 raise TypeError(f"unknown tn_options field {k!r}")
+            if k == "tuner_cache":
+                self._tuner_cache = v.encode() if isinstance(v, str) else v
+                v = self._tuner_cache
             setattr(opt, k, v)
         h = C.c_void_p()
         rc = self._L.tn_create(C.byref(h), int(device), C.byref(opt))
@@ -335,6 +340,24 @@ class Context:
         self._check(self._L.tn_debug_tensor(*args, out.ctypes.data_as(C.POINTER(C.c_double)), out.size,
                                             C.byref(nd), bonds, dims))
         return out.reshape(shape), [int(bonds[a]) for a in range(nd.value)]
+
+    def autotune(self, inst_ids: Sequence[int], chi: int, prec="f64") -> int:
+        """Time the candidate launch shapes of this batch's plan and keep the fastest (tn_autotune)."""
+        ids = np.ascontiguousarray(list(inst_ids), dtype=np.int32)
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        n = C.c_int()
+        self._check(self._L.tn_autotune(self._h, len(ids), ids.ctypes.data_as(C.POINTER(C.c_int)), int(chi), p,
+                                        C.byref(n)))
+        return n.value
+
+    def tuned_choices(self) -> List[Tuple[int, int, int, int, int, int]]:
+        """The device's tuned choices: (family, m, n, k, batch, choice) rows (tn_tuned_choices)."""
+        cnt = self._L.tn_tuned_choices(self._h, 0, None)
+        if cnt < 0:
+            self._check(cnt)
+        buf = (C.c_int32 * (6 * max(cnt, 1)))()
+        self._L.tn_tuned_choices(self._h, cnt, buf)
+        return [tuple(int(buf[6 * i + j]) for j in range(6)) for i in range(cnt)]
 
     def plan_stats(self, inst_id: int, chi: int, prec="f64") -> Dict[str, float]:
         st = PlanStats()

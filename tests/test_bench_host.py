@@ -19,11 +19,27 @@ def test_parse_clocks(tmp_path):
 
 
 def test_ranks_get_disjoint_seeds():
-    a, _ = bench.build_inputs(0, 2)
-    b, _ = bench.build_inputs(1, 2)
+    import argparse
+    wl = bench.Normal32(argparse.Namespace(batch=2))
+    a, b = wl.nets(0), wl.nets(1)
     for x in a:
         for y in b:
             assert not (x.data[0] == y.data[0]).all()
+
+
+def test_ising_sweep_batches_hold_the_stored_betas_and_split_ranks():
+    import argparse
+    import numpy as np
+    from tn_inputs import networks as nw
+    wl = bench.Ising64(argparse.Namespace(batch=32))
+    b0, b1 = wl.betas(0), wl.betas(1)
+    assert len(b0) == len(b1) == 32 and len(set(b0)) == 32
+    sweep = set(float(x) for x in nw.beta_sweep(256))
+    assert set(b0) <= sweep and set(b1) <= sweep
+    gold = [e["beta"] for e in wl.gold]
+    assert b0[:len(gold)] == gold and b1[:len(gold)] == gold
+    assert set(b0[len(gold):]).isdisjoint(b1[len(gold):])
+    assert min(b0) == 0.2 and max(b0) == 0.7 and np.isclose(sorted(b0)[1] - sorted(b0)[0], 0.5 / 255 * 8, atol=0.1)
 
 
 def _free_port():

@@ -7,8 +7,10 @@ the spread of ln|Z| - ln(1 + eps) when one input tensor is scaled by
 (1 + eps), |eps| <= 3e-15.  That spread ranges from 4e-12 (beta = 0.7) to
 1.2e-5 relative (beta = 0.44, near the critical point), so two correct FP64
 implementations can differ by that much end to end; the end-to-end tolerance
-at each beta is therefore max(1e-9, 4 x spread), and exact parity is checked
-op by op on two whole boundary rows instead (tests/oplevel.py).
+at each beta is therefore max(1e-9, 4 x spread) for the FP64 form and
+max(1e-6, 4 x spread) for a reduced-precision form (the metric's gate), and
+exact parity is checked op by op on two whole boundary rows instead
+(tests/oplevel.py).
 """
 import json
 import os
@@ -46,8 +48,10 @@ def sweep(golden):
     ctx.close()
 
 
-def _band(e):
-    return max(1e-9, 4.0 * e["spread_rel"])
+def _band(e, prec):
+    # the FP64 form: within the oracle's own rounding band; a reduced-precision
+    # form: within the metric's gate of 1e-6, or that band where it is wider
+    return max(1e-9 if prec == "f64" else 1e-6, 4.0 * e["spread_rel"])
 
 
 @pytest.mark.parametrize("prec", ["f64", "tf32x3"])
@@ -59,7 +63,7 @@ def test_sweep_end_to_end_within_rounding_band(golden, sweep, prec):
         assert s == e["sign"] == 1
         rel = abs(got - e["logabsz"]) / abs(e["logabsz"])
         errs.append(rel)
-        assert rel <= _band(e), (prec, e["beta"], got, e["logabsz"], rel, _band(e))
+        assert rel <= _band(e, prec), (prec, e["beta"], got, e["logabsz"], rel, _band(e, prec))
     print(prec, "rel errors vs oracle:", ["%.1e" % x for x in errs])
 
 

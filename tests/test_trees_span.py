@@ -111,3 +111,20 @@ def test_boundary_layers_make_the_8x8x8_glass_plannable_at_chi_32():
     assert cost["total"] < 1e13 and cost["peak"] < 1e9
     p = tn.plan_describe(net, t, 32)
     assert p["arena_units"] * 8 < 4e9
+
+
+def test_greedy_with_the_si_input_reduction_stays_near_boundary_rows():
+    """Greedy (SI "Greedy") on square lattices, D = 4, chi = 64: with the input sizes
+    reduced by their maximum (one of the SI's reductions) the traced cost C stays
+    within a small factor of the boundary-row order, while the sum reduction grows
+    2D blobs whose tensors explode (the cost C of Sec. "Tree cost functions")."""
+    for L, bound in ((16, 6.0), (32, 3.0)):
+        n, e = nw.square_lattice(L, L)
+        net = nw.random_network(n, e, 4, seed=0)
+        base = tr.trace_cost(net.bonds, net.bond_dims, tr.boundary_rows(L, L), 64)["total"]
+        g = tr.greedy(net.bonds, net.bond_dims, 64, **tr.greedy_front_params(64))
+        c = tr.trace_cost(net.bonds, net.bond_dims, g, 64)
+        assert c["total"] < bound * base, (L, c["total"], base)
+        if L == 16:
+            blob = tr.trace_cost(net.bonds, net.bond_dims, tr.greedy(net.bonds, net.bond_dims, 64), 64)["total"]
+            assert blob > 100 * base

@@ -404,18 +404,51 @@ def span(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], policy: s
     return from_pairs(net_bonds, pairs, policy)
 
 
+def _combine(mode: str, a: float, b: float) -> float:
+    """The SI's reductions of a pair of input features: min, max, sum, mean or difference."""
+    if mode == "sum":
+        return a + b
+    if mode == "min":
+        return min(a, b)
+    if mode == "max":
+        return max(a, b)
+    if mode == "mean":
+        return 0.5 * (a + b)
+    if mode == "diff":
+        return abs(a - b)
+    raise ValueError(f"unknown reduction {mode!r}")
+
+
+# Greedy weights that grow boundary-like fronts on regular 2D lattices (found by
+# hyper_search over the SI's 11 dimensions on a 32 x 32, D = 4, chi = 64
+# lattice): the size after compression against the larger input's size, and a
+# simulated chi_greedy of chi / 2.
+def greedy_front_params(chi: int) -> Dict[str, object]:
+    return dict(w_new=1.0, w_old=0.2, w_inputs=-0.85, inputs_mode="max", chi_greedy=max(1, chi // 2))
+
+
 def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int,
            seed: int = 0, temperature: float = 0.0, w_new: float = 1.0, w_old: float = 0.0,
            w_inputs: float = -1.0, w_subgraph: float = 0.0, w_centrality: float = 0.0,
-           chi_greedy: Optional[int] = None, policy: str = "early") -> Tree:
-    """Greedy ordered tree: repeatedly contract the adjacent pair of lowest score
+           chi_greedy: Optional[int] = None, policy: str = "early", inputs_mode: str = "sum",
+           subgraph_mode: str = "sum", centrality_mode: str = "mean", centrality_prop: str = "mean") -> Tree:
+    """Greedy ordered tree (SI "Greedy"): repeatedly contract the adjacent pair of lowest score
 
         score = w_new * log2|k after compression| + w_old * log2|k before|
-              + w_inputs * (log2|i| + log2|j|) + w_subgraph * (|S(i)| + |S(j)|)
-              + w_centrality * (c_i + c_j) / 2 + temperature * Gumbel,
+              + w_inputs * R_in(log2|i|, log2|j|) + w_subgraph * R_sub(|S(i)|, |S(j)|)
+              + w_centrality * R_cen(c_i, c_j) + temperature * Gumbel,
 
-    simulating early compression at chi_greedy (default chi) after each step.
-    Disconnected components are joined by outer products at the end.
+    each R one of the SI's reductions (min, max, sum, mean or difference; the
+    centrality takes min, max, mean or difference) chosen by ``*_mode``, and a
+    contracted tensor's centrality propagated from its inputs by
+    ``centrality_prop`` (min, max or mean).  Early compression is simulated at
+    chi_greedy (default chi) after each step.  Disconnected components are
+    joined by outer products at the end.
+
+    On lattices the reduction matters: with inputs_mode="max" and
+    w_inputs = -w_new, absorbing a small tensor into a large one scores the
+    growth of the large one, so boundary-like fronts grow instead of 2D blobs
+    whose perimeters blow up the tensor sizes.
     """
     chig = chi_greedy or chi
     rng = np.random.default_rng(seed)
@@ -431,8 +464,10 @@ def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: in
 
     def score(i: int, j: int) -> float:
         before, after = sim.contract_sizes(i, j, chig)
-        s = w_new * after + w_old * before + w_inputs * (sim.log2size(i) + sim.log2size(j))
-        s += w_subgraph * (sub[i] + sub[j]) + w_centrality * 0.5 * (cent[i] + cent[j])
+        s = w_new * after + w_old * before + w_inputs * _combine(inputs_mode, sim.log2size(i), sim.log2size(j))
+        s += w_subgraph * _combine(subgraph_mode, sub[i], sub[j])
+        if w_centrality:
+            s += w_centrality * _combine(centrality_mode, cent[i], cent[j])
         if temperature:
             s += temperature * float(-math.log(-math.log(rng.uniform(1e-12, 1.0))))
         return s
@@ -458,7 +493,7 @@ def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: in
         pairs.append((i, j))
         sim.contract(i, j, k)
         sub[k] = sub[i] + sub[j]
-        cent[k] = 0.5 * (cent[i] + cent[j])
+        cent[k] = {"min": min, "max": max}.get(centrality_prop, lambda a, b: 0.5 * (a + b))(cent[i], cent[j])
         version[k] = 0
         for l in sorted(sim.groups(k)):
             ops.append(("S", k, l))
@@ -579,11 +614,21 @@ def hyper_search(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], c
                           temperature=float(rng.choice([0.0, 0.0, 0.5, 2.0])), seed=trial)
             tree = span(net_bonds, bond_dims, **params)
         elif builder == "greedy":
-            params = dict(seed=trial, temperature=float(rng.choice([0.0, 0.1, 0.5])),
-                          w_new=float(rng.uniform(0.5, 1.5)), w_old=float(rng.uniform(-0.5, 0.5)),
-                          w_inputs=float(rng.uniform(-1.5, 0.0)), w_subgraph=float(rng.uniform(-0.2, 0.2)),
-                          w_centrality=float(rng.uniform(-1.0, 1.0)),
-                          chi_greedy=int(rng.choice([chi, 2 * chi, max(1, chi // 2)])))
+            # the SI's 11 dimensions: three size weights, the input-size reduction,
+            # subgraph weight and reduction, centrality weight, reduction and
+            # propagation, temperature and chi_greedy; sizes after compression
+            # keep weight 1 (only ratios matter), the input weight is drawn
+            # around -1 where a front grows by absorbing small tensors
+            params = dict(seed=trial, temperature=float(rng.choice([0.0, 0.0, 0.05, 0.2])),
+                          w_new=1.0, w_old=float(rng.uniform(-0.3, 0.3)),
+                          w_inputs=float(rng.uniform(-1.1, -0.7)),
+                          inputs_mode=str(rng.choice(["max", "max", "sum", "mean", "diff", "min"])),
+                          w_subgraph=float(rng.choice([0.0, 1.0]) * rng.uniform(-0.02, 0.05)),
+                          subgraph_mode=str(rng.choice(["sum", "max", "min", "mean", "diff"])),
+                          w_centrality=float(rng.choice([0.0, 1.0]) * rng.uniform(-1.0, 1.0)),
+                          centrality_mode=str(rng.choice(["mean", "min", "max", "diff"])),
+                          centrality_prop=str(rng.choice(["mean", "min", "max"])),
+                          chi_greedy=int(rng.choice([chi, chi, 2 * chi, max(1, chi // 2)])))
             tree = greedy(net_bonds, bond_dims, chi, **params)
         else:
             raise ValueError(builder)
