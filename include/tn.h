@@ -130,7 +130,12 @@ typedef struct {
  *                      tn_create its choices are loaded if the file exists
  *                      and was written on the same GPU model (a file from
  *                      another model is ignored; an unreadable one gives
- *                      TN_EFORMAT); tn_autotune rewrites it. */
+ *                      TN_EFORMAT); tn_autotune rewrites it.
+ *   sequential_groups  1: a tn_contract_approx call whose instances fall into
+ *                      several groups (different structures or trees) runs
+ *                      the groups one after the other; 0 (default): as
+ *                      concurrent branches of one pass (see
+ *                      tn_contract_approx).  Results are identical. */
 typedef struct {
   int32_t struct_size;
   int32_t graph_mode;
@@ -140,6 +145,8 @@ typedef struct {
   int32_t debug_tc_give_up;
   int32_t reserved;
   const char* tuner_cache;
+  int32_t sequential_groups;
+  int32_t reserved2;
 } tn_options;
 
 /* Default options (struct_size = sizeof(tn_options)). */
@@ -222,7 +229,13 @@ int tn_load_tree_file(tn_ctx* ctx, int net_id, const char* path, int* inst_id);
 
 /* Approximately contract n_inst instances at bond dimension chi (>= 1) in the
  * given arithmetic form.  Instances with identical network structure and tree
- * run as one batch.  logabsz_out[n] = ln|Z_n| (-inf when Z_n == 0) and
+ * run as one batch (a group: every launch covers the whole group).  Several
+ * groups -- instances of uneven trees, such as different random graphs --
+ * run as concurrent branches of one pass: each group has its own slice of
+ * the device buffers and its own stream pair, forked from and joined back to
+ * the context's stream; with graph mode the multi-group pass is captured as
+ * one CUDA graph on its second call and replayed after (batching across
+ * instances of different shapes, Sec. on beta sweeps and instances).  logabsz_out[n] = ln|Z_n| (-inf when Z_n == 0) and
  * sign_out[n] in {-1, 0, +1} are caller-allocated host arrays of n_inst.
  * Synchronises the context's stream before returning. */
 int tn_contract_approx(tn_ctx* ctx, int n_inst, const int* inst_ids, int chi, int prec,

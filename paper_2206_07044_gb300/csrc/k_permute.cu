@@ -2,12 +2,14 @@
 // (left, shared) or (shared, right) order.  Pure data movement, HBM-bound:
 // 2 * |T| * 8 bytes per tensor.
 //
-// Two paths:
-//  * the output's innermost axis is the input's innermost axis: a gather whose
-//    reads and writes are both contiguous runs along that axis;
-//  * otherwise a 32 x 32 shared-memory tile over (input innermost axis,
-//    input axis that becomes the output's innermost), so that both the load
-//    and the store are coalesced; the other axes index tiles.
+// The permutation is first reduced to canonical form (size-1 axes dropped,
+// input axes that stay adjacent and in order merged), then:
+//  * a 32 x 32 shared-memory tile over (input innermost axis, input axis that
+//    becomes the output's innermost) when both are at least 16 long, so that
+//    both the load and the store are coalesced; the other axes index tiles;
+//  * otherwise a gather: one thread per output element (coalesced stores,
+//    32-bit index arithmetic), the loads in runs along the preserved or short
+//    innermost axes.
 #include "tn_kernels.h"
 
 namespace tnk {
@@ -20,20 +22,23 @@ struct PermParams {
   int64_t in_stride_of_out[kMaxDims];  // input stride of output axis a
 };
 
+template <typename I>
 __global__ void permute_gather(const double* __restrict__ in, int64_t in_bs, double* __restrict__ out,
                                int64_t out_bs, PermParams p) {
   const int b = blockIdx.y;
   const double* src = in + (int64_t)b * in_bs;
   double* dst = out + (int64_t)b * out_bs;
-  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < p.n;
-       o += (int64_t)gridDim.x * blockDim.x) {
-    int64_t rem = o, off = 0;
-    for (int a = p.nd - 1; a >= 0; --a) {
-      int64_t c = rem % p.out_dims[a];
-      rem /= p.out_dims[a];
-      off += c * p.in_stride_of_out[a];
+  const I n = (I)p.n;
+  for (I o = (I)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (I)gridDim.x * blockDim.x) {
+    I rem = o, off = 0;
+    for (int a = p.nd - 1; a > 0; --a) {
+      const I d = (I)p.out_dims[a];
+      const I q = rem / d;
+      off += (rem - q * d) * (I)p.in_stride_of_out[a];
+      rem = q;
     }
-    dst[o] = src[off];
+    off += rem * (I)p.in_stride_of_out[0];
+    dst[o] = __ldg(src + off);
   }
 }
 
@@ -85,9 +90,58 @@ __global__ void permute_tiled(const double* __restrict__ in, int64_t in_bs, doub
 
 }  // namespace
 
-cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t out_bs, int nd,
-                        const int64_t* in_dims, const int* perm, int batch, cudaStream_t s) {
-  if (nd > kMaxDims || batch <= 0) return cudaErrorInvalidValue;
+cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t out_bs, int nd0,
+                        const int64_t* in_dims0, const int* perm0, int batch, cudaStream_t s) {
+  if (nd0 > kMaxDims || batch <= 0) return cudaErrorInvalidValue;
+  // Canonical form: drop size-1 axes, then merge input axes a, a+1 that stay
+  // adjacent and in order in the output (they move as one axis).  The
+  // boundary contraction's permutes shrink to 2-3 axes this way.
+  int keep[kMaxDims], nk = 0, new_of[kMaxDims];
+  for (int a = 0; a < nd0; ++a) {
+    new_of[a] = -1;
+    if (in_dims0[a] > 1) {
+      new_of[a] = nk;
+      keep[nk++] = a;
+    }
+  }
+  int64_t dims1[kMaxDims];
+  int perm1[kMaxDims], np1 = 0;
+  for (int q = 0; q < nk; ++q) dims1[q] = in_dims0[keep[q]];
+  for (int a = 0; a < nd0; ++a)
+    if (new_of[perm0[a]] >= 0) perm1[np1++] = new_of[perm0[a]];
+  // merge: group output positions into runs of consecutive input axes
+  int64_t in_dims[kMaxDims];
+  int perm[kMaxDims], nd = 0;
+  {
+    int64_t gdim[kMaxDims];
+    int gfirst[kMaxDims], ng = 0;
+    for (int q = 0; q < np1;) {
+      int r = q + 1;
+      while (r < np1 && perm1[r] == perm1[r - 1] + 1) ++r;
+      int64_t d = 1;
+      for (int t = q; t < r; ++t) d *= dims1[perm1[t]];
+      gdim[ng] = d;
+      gfirst[ng] = perm1[q];
+      ++ng;
+      q = r;
+    }
+    // input order of the groups: by their first input axis
+    int order[kMaxDims];
+    for (int g = 0; g < ng; ++g) order[g] = g;
+    for (int i = 1; i < ng; ++i)
+      for (int j = i; j > 0 && gfirst[order[j - 1]] > gfirst[order[j]]; --j) {
+        int t = order[j];
+        order[j] = order[j - 1];
+        order[j - 1] = t;
+      }
+    int in_pos[kMaxDims];
+    for (int i = 0; i < ng; ++i) {
+      in_dims[i] = gdim[order[i]];
+      in_pos[order[i]] = i;
+    }
+    for (int g = 0; g < ng; ++g) perm[g] = in_pos[g];
+    nd = ng;
+  }
   int64_t n = 1;
   int64_t in_stride[kMaxDims];
   for (int a = nd - 1; a >= 0; --a) {
@@ -95,6 +149,12 @@ cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t ou
     n *= in_dims[a];
   }
   if (n == 0) return cudaSuccess;
+  if (nd == 0) {  // a scalar: copy the single element
+    nd = 1;
+    in_dims[0] = 1;
+    in_stride[0] = 1;
+    perm[0] = 0;
+  }
   int64_t out_dims[kMaxDims], out_stride[kMaxDims];
   for (int a = 0; a < nd; ++a) out_dims[a] = in_dims[perm[a]];
   {
@@ -104,14 +164,11 @@ cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t ou
       acc *= out_dims[a];
     }
   }
-  // drop size-1 axes when deciding the path
-  int last_in = -1;
-  for (int a = nd - 1; a >= 0; --a)
-    if (in_dims[a] > 1) { last_in = a; break; }
-  int last_out = -1;
-  for (int a = nd - 1; a >= 0; --a)
-    if (out_dims[a] > 1) { last_out = a; break; }
-  if (last_in < 0 || last_out < 0 || perm[last_out] == last_in || nd == 1) {
+  const int ax_x = nd - 1, ax_y = perm[nd - 1];
+  const bool tiled = ax_y != ax_x && in_dims[ax_x] >= 16 && in_dims[ax_y] >= 16;
+  if (!tiled) {
+    // gather: each thread writes one output element (coalesced), reads the input
+    // at its offset; the innermost run moves contiguously when it is preserved
     PermParams p{};
     p.nd = nd;
     p.n = n;
@@ -120,13 +177,15 @@ cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t ou
       p.in_stride_of_out[a] = in_stride[perm[a]];
     }
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
+    if (blocks > 8192) blocks = 8192;
     dim3 grid((unsigned)blocks, (unsigned)batch);
-    permute_gather<<<grid, 256, 0, s>>>(in, in_bs, out, out_bs, p);
+    if (n < (int64_t(1) << 31))
+      permute_gather<int32_t><<<grid, 256, 0, s>>>(in, in_bs, out, out_bs, p);
+    else
+      permute_gather<int64_t><<<grid, 256, 0, s>>>(in, in_bs, out, out_bs, p);
     return cudaGetLastError();
   }
-  // tiled path: X = input axis last_in, Y = input axis perm[last_out]
-  const int ax_x = last_in, ax_y = perm[last_out];
+  // tiled path: X = the input's innermost axis, Y = the input axis that becomes the output's innermost
   int out_pos_of_in[kMaxDims];
   for (int a = 0; a < nd; ++a) out_pos_of_in[perm[a]] = a;
   TileParams p{};
@@ -137,7 +196,7 @@ cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t ou
   p.n_outer = 0;
   int64_t n_outer_total = 1;
   for (int a = 0; a < nd; ++a) {
-    if (a == ax_x || a == ax_y || in_dims[a] == 1) continue;
+    if (a == ax_x || a == ax_y) continue;
     p.outer_dims[p.n_outer] = in_dims[a];
     p.outer_in_stride[p.n_outer] = in_stride[a];
     p.outer_out_stride[p.n_outer] = out_stride[out_pos_of_in[a]];

@@ -211,7 +211,9 @@ __global__ void __launch_bounds__(kMaxJacThreads) block_jacobi_kernel(JacArgs<T>
   int* cnt = p.ws + kWsInts * bidx;
   {
     const T fro2 = cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
-    const T eps64 = T(64) * (sizeof(T) == sizeof(double) ? T(DBL_EPSILON) : T(FLT_EPSILON));
+    // the rounding-floor test serves the FP64 polish; the FP32 preconditioner
+    // keeps the plain relative test (its floor would be far coarser)
+    const T eps64 = sizeof(T) == sizeof(double) ? T(64) * T(DBL_EPSILON) : T(0);
     p.floor2 = p.floor_rel * p.floor_rel * fro2;
     p.noise2 = eps64 * eps64 * fro2;
   }
@@ -359,7 +361,9 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
   int* cnt = p.ws + kWsInts * bidx;
   {
     const T fro2 = cluster_fro2(cl, G, m, n, rank, P, reinterpret_cast<double*>(cnt + 8));
-    const T eps64 = T(64) * (sizeof(T) == sizeof(double) ? T(DBL_EPSILON) : T(FLT_EPSILON));
+    // the rounding-floor test serves the FP64 polish; the FP32 preconditioner
+    // keeps the plain relative test (its floor would be far coarser)
+    const T eps64 = sizeof(T) == sizeof(double) ? T(64) * T(DBL_EPSILON) : T(0);
     p.floor2 = p.floor_rel * p.floor_rel * fro2;
     p.noise2 = eps64 * eps64 * fro2;
   }

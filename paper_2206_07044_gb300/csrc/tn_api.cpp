@@ -125,6 +125,29 @@ struct tn_ctx {
   cudaStream_t cap = nullptr;
   std::map<GraphKey, GraphRec> graphs;
   int64_t graph_captured = 0, graph_replays = 0, graph_refused = 0;
+  // concurrent groups: instances whose trees differ run as parallel branches
+  // (one stream pair per group) over slices of one set of buffers
+  struct Multi {
+    double* arena = nullptr;
+    size_t arena_bytes = 0;
+    double* inbuf = nullptr;
+    size_t inbuf_bytes = 0;
+    long long* expo = nullptr;
+    int* status = nullptr;
+    int* jac_ws = nullptr;
+    unsigned long long* maxbits = nullptr;
+    double* out_log = nullptr;
+    int* out_sign = nullptr;
+    int* tc_err = nullptr;
+    int cap_inst = 0, cap_groups = 0;
+    std::vector<cudaStream_t> streams, sides;
+    std::vector<cudaEvent_t> ev_fork, ev_join, ev_done;
+    cudaEvent_t ev_start = nullptr;
+    uint64_t gen = 0;
+    std::map<std::vector<int>, GraphRec> graphs;  // key: (plan serial, n members, members...) per group, then gen
+  } multi;
+  int64_t concurrent_runs = 0;
+  int concurrent_groups = 1;  // run groups with different trees as concurrent branches
   // tn_debug_tensor: where the last partial run stopped (its plan, members and
   // buffer generation), so that a later call with a later stop continues from there
   uint64_t dbg_serial = 0, dbg_gen = 0;
@@ -537,6 +560,195 @@ int run_group(tn_ctx* c, const tnp::Plan& plan, const std::vector<int>& members,
   return TN_OK;
 }
 
+// Forward passes of several groups (instances whose network structure and
+// tree differ between groups) as concurrent branches: every group gets a
+// slice of one arena / input block / scratch set and its own stream pair; the
+// main stream forks to all of them and joins them back.  With graph mode the
+// whole multi-group pass is captured on the second call (one graph whose
+// branches are the groups' schedules) and replayed after.  The kernels, shapes
+// and data of each group are those of run_group, so results are identical to
+// running the groups one after the other.
+int run_groups_concurrent(tn_ctx* c, const std::vector<const tnp::Plan*>& plans,
+                          const std::vector<std::vector<int>>& groups, std::vector<std::vector<double>>* logabs,
+                          std::vector<std::vector<int>>* sign) {
+  auto& M = c->multi;
+  const int G = (int)groups.size();
+  c->dbg_stop = -2;
+  std::vector<int64_t> a_off(G), i_off(G), o_off(G);
+  int64_t a_tot = 0, i_tot = 0, o_tot = 0;
+  for (int g = 0; g < G; ++g) {
+    const int batch = (int)groups[g].size();
+    if (batch > 65535) return fail(c, TN_EINVAL, "more than 65535 instances in one batch");
+    const tnp::Structure& st = c->nets[c->insts[groups[g][0]].net].st;
+    a_off[g] = a_tot;
+    i_off[g] = i_tot;
+    o_off[g] = o_tot;
+    a_tot += (std::max<int64_t>(plans[g]->arena_units, 1) * batch + 31) / 32 * 32;
+    i_tot += (std::max<int64_t>(st.in_total, 1) * batch + 31) / 32 * 32;
+    o_tot += batch;
+  }
+  cudaError_t e;
+  const void* before[3] = {M.arena, M.inbuf, M.expo};
+  if ((e = ensure(&M.arena, &M.arena_bytes, sizeof(double) * (size_t)a_tot)) != cudaSuccess)
+    return fail(c, TN_ENOMEM, "arena allocation of " + std::to_string(8 * a_tot) + " bytes failed");
+  if ((e = ensure(&M.inbuf, &M.inbuf_bytes, sizeof(double) * (size_t)i_tot)) != cudaSuccess)
+    return fail(c, TN_ENOMEM, "input buffer allocation failed");
+  if (M.cap_inst < o_tot || M.cap_groups < G) {
+    cudaFree(M.expo);
+    cudaFree(M.status);
+    cudaFree(M.jac_ws);
+    cudaFree(M.maxbits);
+    cudaFree(M.out_log);
+    cudaFree(M.out_sign);
+    cudaFree(M.tc_err);
+    M.expo = nullptr;
+    M.cap_inst = M.cap_groups = 0;
+    const size_t n = (size_t)o_tot;
+    if (cudaMalloc(&M.expo, sizeof(long long) * n) != cudaSuccess ||
+        cudaMalloc(&M.status, sizeof(int) * n) != cudaSuccess ||
+        cudaMalloc(&M.jac_ws, sizeof(int) * 64 * n) != cudaSuccess ||
+        cudaMalloc(&M.maxbits, sizeof(unsigned long long) * n) != cudaSuccess ||
+        cudaMalloc(&M.out_log, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&M.out_sign, sizeof(int) * n) != cudaSuccess ||
+        cudaMalloc(&M.tc_err, sizeof(int) * (size_t)G) != cudaSuccess)
+      return fail(c, TN_ENOMEM, "scratch allocation failed");
+    M.cap_inst = (int)o_tot;
+    M.cap_groups = G;
+  }
+  if (before[0] != M.arena || before[1] != M.inbuf || before[2] != M.expo) {
+    for (auto& gx : M.graphs)
+      if (gx.second.exec) cudaGraphExecDestroy(gx.second.exec);
+    M.graphs.clear();
+    ++M.gen;
+  }
+  while ((int)M.streams.size() < G) {
+    cudaStream_t a = nullptr, b = nullptr;
+    cudaEvent_t f = nullptr, j = nullptr, d = nullptr;
+    if (cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d, cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, TN_ECUDA, "stream creation failed");
+    M.streams.push_back(a);
+    M.sides.push_back(b);
+    M.ev_fork.push_back(f);
+    M.ev_join.push_back(j);
+    M.ev_done.push_back(d);
+  }
+  if (!M.ev_start && cudaEventCreateWithFlags(&M.ev_start, cudaEventDisableTiming) != cudaSuccess)
+    return fail(c, TN_ECUDA, "event creation failed");
+
+  auto enqueue = [&](cudaStream_t s0) -> int {
+    if (cudaEventRecord(M.ev_start, s0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "fork");
+    for (int g = 0; g < G; ++g) {
+      const tnp::Plan& plan = *plans[g];
+      const std::vector<int>& members = groups[g];
+      const int batch = (int)members.size();
+      const tnp::Structure& st = c->nets[c->insts[members[0]].net].st;
+      tnx::ExecEnv env;
+      env.inbuf = M.inbuf + i_off[g];
+      env.arena = M.arena + a_off[g];
+      env.batch = batch;
+      env.ds = tnk::DevState{M.expo + o_off[g], M.status + o_off[g]};
+      env.jac_ws = M.jac_ws + 64 * o_off[g];
+      env.maxbits = M.maxbits + o_off[g];
+      env.out_log = M.out_log + o_off[g];
+      env.out_sign = M.out_sign + o_off[g];
+      env.tc_err = M.tc_err + g;
+      env.jac_max_sweeps = c->opt_max_sweeps;
+      env.tc_give_up = c->opt_tc_give_up;
+      cudaStream_t s = M.streams[g];
+      cudaError_t e2 = cudaStreamWaitEvent(s, M.ev_start, 0);
+      for (int b = 0; b < batch && e2 == cudaSuccess; ++b) {
+        const NetRec& nr = c->nets[c->insts[members[b]].net];
+        e2 = cudaMemcpyAsync(env.inbuf + (size_t)b * st.in_total, nr.d_data, sizeof(double) * st.in_total,
+                             cudaMemcpyDeviceToDevice, s);
+      }
+      if (e2 == cudaSuccess) e2 = cudaMemsetAsync(env.ds.expo, 0, sizeof(long long) * batch, s);
+      if (e2 == cudaSuccess) e2 = cudaMemsetAsync(env.ds.status, 0, sizeof(int) * batch, s);
+      if (e2 == cudaSuccess) e2 = cudaMemsetAsync(env.tc_err, 0, sizeof(int), s);
+      if (e2 != cudaSuccess) return cuda_fail(c, e2, "gather inputs");
+      bool side_open = false;
+      for (const tnp::Step& stp : plan.steps) {
+        if (stp.join && side_open) {
+          cudaStreamWaitEvent(s, M.ev_join[g], 0);
+          side_open = false;
+        }
+        cudaStream_t ss = s;
+        if (stp.lane == 1) {
+          cudaEventRecord(M.ev_fork[g], s);
+          cudaStreamWaitEvent(M.sides[g], M.ev_fork[g], 0);
+          ss = M.sides[g];
+        }
+        e2 = tnx::exec_step(stp, env, ss);
+        if (e2 != cudaSuccess)
+          return fail(c, TN_ECUDA, std::string("launch of ") + kFamily[stp.kind] + " (tree op " +
+                                       std::to_string(stp.op_index) + ") failed: " + cudaGetErrorString(e2));
+        if (stp.lane == 1) {
+          cudaEventRecord(M.ev_join[g], ss);
+          side_open = true;
+        }
+      }
+      if (side_open) cudaStreamWaitEvent(s, M.ev_join[g], 0);
+      cudaEventRecord(M.ev_done[g], s);
+      if (cudaStreamWaitEvent(s0, M.ev_done[g], 0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "join");
+    }
+    return TN_OK;
+  };
+
+  cudaStream_t s = c->stream;
+  GraphRec* gr = nullptr;
+  if (c->graph_mode) {
+    std::vector<int> key;
+    for (int g = 0; g < G; ++g) {
+      key.push_back((int)plans[g]->serial);
+      key.push_back((int)groups[g].size());
+      key.insert(key.end(), groups[g].begin(), groups[g].end());
+    }
+    key.push_back((int)M.gen);
+    auto it = M.graphs.find(key);
+    if (it == M.graphs.end()) {
+      M.graphs.emplace(key, GraphRec{});  // first call: eager (still concurrent); captured on the next
+    } else {
+      gr = &it->second;
+      if (!gr->exec && !gr->failed) capture_graph(c, gr, enqueue);
+    }
+  }
+  if (gr && gr->exec) {
+    e = cudaGraphLaunch(gr->exec, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    ++c->graph_replays;
+  } else {
+    const int rc = enqueue(s);
+    if (rc != TN_OK) return rc;
+  }
+  ++c->concurrent_runs;
+  std::vector<double> hl(o_tot);
+  std::vector<int> hs(o_tot), hst(o_tot), htc(G);
+  e = cudaMemcpyAsync(hl.data(), M.out_log, sizeof(double) * o_tot, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), M.out_sign, sizeof(int) * o_tot, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), M.status, sizeof(int) * o_tot, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(htc.data(), M.tc_err, sizeof(int) * G, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+  for (int g = 0; g < G; ++g)
+    if (htc[g]) return fail(c, TN_ETIMEOUT, "a tensor-core GEMM's bounded wait ran out");
+  int worst = 0;
+  logabs->assign(G, {});
+  sign->assign(G, {});
+  for (int g = 0; g < G; ++g)
+    for (size_t b = 0; b < groups[g].size(); ++b) {
+      (*logabs)[g].push_back(hl[o_off[g] + b]);
+      (*sign)[g].push_back(hs[o_off[g] + b]);
+      if (hst[o_off[g] + b] != 0 && worst == 0) worst = hst[o_off[g] + b];
+    }
+  if (worst == -9) return fail(c, TN_ENOCONV, "Jacobi SVD did not converge");
+  if (worst == -7) return fail(c, TN_ENONFINITE, "non-finite intermediate");
+  if (worst != 0) return fail(c, TN_ECUDA, "device status " + std::to_string(worst));
+  return TN_OK;
+}
+
 bool read_file(const char* path, std::string* out) {
   std::ifstream f(path, std::ios::binary);
   if (!f) return false;
@@ -620,7 +832,8 @@ int tn_create(tn_ctx** out, int device, const tn_options* opt) {
     o = *opt;
   }
   if (o.graph_mode < 0 || o.graph_mode > 1 || o.grad_segments < 0 || o.debug_max_sweeps < 0 ||
-      !(o.tape_budget_bytes >= 0.0) || o.debug_tc_give_up < 0 || o.debug_tc_give_up > 1)
+      !(o.tape_budget_bytes >= 0.0) || o.debug_tc_give_up < 0 || o.debug_tc_give_up > 1 ||
+      o.sequential_groups < 0 || o.sequential_groups > 1)
     return TN_EINVAL;
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TN_ECUDA;
@@ -632,6 +845,7 @@ int tn_create(tn_ctx** out, int device, const tn_options* opt) {
   c->tape_budget = o.tape_budget_bytes;
   c->opt_max_sweeps = o.debug_max_sweeps;
   c->opt_tc_give_up = o.debug_tc_give_up != 0;
+  c->concurrent_groups = o.sequential_groups ? 0 : 1;
   if (o.tuner_cache && *o.tuner_cache) {
     c->tuner_cache = o.tuner_cache;
     DeviceGuard g(device);
@@ -663,6 +877,26 @@ void tn_destroy(tn_ctx* c) {
   cudaFree(c->tc_err);
   for (auto& gx : c->graphs)
     if (gx.second.exec) cudaGraphExecDestroy(gx.second.exec);
+  {
+    auto& M = c->multi;
+    for (auto& gx : M.graphs)
+      if (gx.second.exec) cudaGraphExecDestroy(gx.second.exec);
+    cudaFree(M.arena);
+    cudaFree(M.inbuf);
+    cudaFree(M.expo);
+    cudaFree(M.status);
+    cudaFree(M.jac_ws);
+    cudaFree(M.maxbits);
+    cudaFree(M.out_log);
+    cudaFree(M.out_sign);
+    cudaFree(M.tc_err);
+    for (auto x : M.streams) cudaStreamDestroy(x);
+    for (auto x : M.sides) cudaStreamDestroy(x);
+    for (auto x : M.ev_fork) cudaEventDestroy(x);
+    for (auto x : M.ev_join) cudaEventDestroy(x);
+    for (auto x : M.ev_done) cudaEventDestroy(x);
+    if (M.ev_start) cudaEventDestroy(M.ev_start);
+  }
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -812,6 +1046,8 @@ int tn_contract_approx(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int 
     if (inst_ids[q] < 0 || inst_ids[q] >= (int)c->insts.size()) return fail(c, TN_EINVAL, "unknown instance id");
   DeviceGuard g(c->device);
   std::vector<bool> done(n_inst, false);
+  std::vector<std::vector<int>> groups, poss;
+  std::vector<const tnp::Plan*> plans;
   for (int q = 0; q < n_inst; ++q) {
     if (done[q]) continue;
     std::vector<int> members, pos;
@@ -824,13 +1060,35 @@ int tn_contract_approx(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int 
     int rc = TN_OK;
     const tnp::Plan* plan = get_plan(c, inst_ids[q], chi, prec, &rc);
     if (!plan) return rc;
-    std::vector<double> lg(members.size());
-    std::vector<int> sg(members.size());
-    rc = run_group(c, *plan, members, lg.data(), sg.data());
+    groups.push_back(members);
+    poss.push_back(pos);
+    plans.push_back(plan);
+  }
+  // (two groups could share one cached plan slot only through a hash
+  // collision of their structures and trees; they then run one after the other)
+  bool distinct = true;
+  for (size_t a = 0; a < plans.size(); ++a)
+    for (size_t b = a + 1; b < plans.size(); ++b) distinct = distinct && plans[a] != plans[b];
+  if (groups.size() >= 2 && !c->profile && c->concurrent_groups && distinct) {
+    std::vector<std::vector<double>> lg;
+    std::vector<std::vector<int>> sg;
+    const int rc = run_groups_concurrent(c, plans, groups, &lg, &sg);
     if (rc != TN_OK) return rc;
-    for (size_t m = 0; m < members.size(); ++m) {
-      logabsz_out[pos[m]] = lg[m];
-      sign_out[pos[m]] = sg[m];
+    for (size_t gi = 0; gi < groups.size(); ++gi)
+      for (size_t m = 0; m < groups[gi].size(); ++m) {
+        logabsz_out[poss[gi][m]] = lg[gi][m];
+        sign_out[poss[gi][m]] = sg[gi][m];
+      }
+    return TN_OK;
+  }
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    std::vector<double> lg(groups[gi].size());
+    std::vector<int> sg(groups[gi].size());
+    const int rc = run_group(c, *plans[gi], groups[gi], lg.data(), sg.data());
+    if (rc != TN_OK) return rc;
+    for (size_t m = 0; m < groups[gi].size(); ++m) {
+      logabsz_out[poss[gi][m]] = lg[m];
+      sign_out[poss[gi][m]] = sg[m];
     }
   }
   return TN_OK;

@@ -51,9 +51,12 @@ def walk(ctx, ids, tree, chi, ops, whiches, tol_c=1e-12, tol_s=1e-10, min_gap=1e
     out = {"c_ops": 0, "s_ops": 0, "ambiguous": 0, "max_c": 0.0, "max_s": 0.0}
     for r in ops:
         op = tree.ops[r]
+        # every instance's inputs first (state after op r - 1), then the outputs:
+        # the stops never go backwards, so each debug call continues the last one
+        inputs = {w: (ctx.debug_tensor(ids, w, chi, r - 1, op[1]), ctx.debug_tensor(ids, w, chi, r - 1, op[2]))
+                  for w in whiches}
         for w in whiches:
-            ti, bi = ctx.debug_tensor(ids, w, chi, r - 1, op[1])
-            tj, bj = ctx.debug_tensor(ids, w, chi, r - 1, op[2])
+            (ti, bi), (tj, bj) = inputs[w]
             if op[0] == "C":
                 tk, bk = ctx.debug_tensor(ids, w, chi, r, op[3])
                 want, bw = approx.contract_pair(ti, bi, tj, bj)
