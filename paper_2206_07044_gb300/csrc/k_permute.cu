@@ -15,6 +15,8 @@
 namespace tnk {
 namespace {
 
+constexpr int kMaxPermAxes = 64;  // axes of a permute before canonicalization
+
 struct PermParams {
   int nd;
   int64_t n;                      // elements per batch
@@ -92,11 +94,13 @@ __global__ void permute_tiled(const double* __restrict__ in, int64_t in_bs, doub
 
 cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t out_bs, int nd0,
                         const int64_t* in_dims0, const int* perm0, int batch, cudaStream_t s) {
-  if (nd0 > kMaxDims || batch <= 0) return cudaErrorInvalidValue;
+  // intermediates may carry more bonds than an input tensor (kMaxDims); the
+  // canonical form below must fit the kernels' kMaxDims axes
+  if (nd0 > kMaxPermAxes || batch <= 0) return cudaErrorInvalidValue;
   // Canonical form: drop size-1 axes, then merge input axes a, a+1 that stay
   // adjacent and in order in the output (they move as one axis).  The
   // boundary contraction's permutes shrink to 2-3 axes this way.
-  int keep[kMaxDims], nk = 0, new_of[kMaxDims];
+  int keep[kMaxPermAxes], nk = 0, new_of[kMaxPermAxes];
   for (int a = 0; a < nd0; ++a) {
     new_of[a] = -1;
     if (in_dims0[a] > 1) {
@@ -104,17 +108,17 @@ cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t ou
       keep[nk++] = a;
     }
   }
-  int64_t dims1[kMaxDims];
-  int perm1[kMaxDims], np1 = 0;
+  int64_t dims1[kMaxPermAxes];
+  int perm1[kMaxPermAxes], np1 = 0;
   for (int q = 0; q < nk; ++q) dims1[q] = in_dims0[keep[q]];
   for (int a = 0; a < nd0; ++a)
     if (new_of[perm0[a]] >= 0) perm1[np1++] = new_of[perm0[a]];
   // merge: group output positions into runs of consecutive input axes
-  int64_t in_dims[kMaxDims];
-  int perm[kMaxDims], nd = 0;
+  int64_t in_dims[kMaxPermAxes];
+  int perm[kMaxPermAxes], nd = 0;
   {
-    int64_t gdim[kMaxDims];
-    int gfirst[kMaxDims], ng = 0;
+    int64_t gdim[kMaxPermAxes];
+    int gfirst[kMaxPermAxes], ng = 0;
     for (int q = 0; q < np1;) {
       int r = q + 1;
       while (r < np1 && perm1[r] == perm1[r - 1] + 1) ++r;
@@ -126,7 +130,7 @@ cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t ou
       q = r;
     }
     // input order of the groups: by their first input axis
-    int order[kMaxDims];
+    int order[kMaxPermAxes];
     for (int g = 0; g < ng; ++g) order[g] = g;
     for (int i = 1; i < ng; ++i)
       for (int j = i; j > 0 && gfirst[order[j - 1]] > gfirst[order[j]]; --j) {
@@ -134,7 +138,7 @@ cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t ou
         order[j] = order[j - 1];
         order[j - 1] = t;
       }
-    int in_pos[kMaxDims];
+    int in_pos[kMaxPermAxes];
     for (int i = 0; i < ng; ++i) {
       in_dims[i] = gdim[order[i]];
       in_pos[order[i]] = i;
@@ -142,6 +146,7 @@ cudaError_t permute_f64(const double* in, int64_t in_bs, double* out, int64_t ou
     for (int g = 0; g < ng; ++g) perm[g] = in_pos[g];
     nd = ng;
   }
+  if (nd > kMaxDims) return cudaErrorInvalidValue;
   int64_t n = 1;
   int64_t in_stride[kMaxDims];
   for (int a = nd - 1; a >= 0; --a) {

@@ -42,13 +42,14 @@ def row_ops(lx, y):
 def walk(ctx, ids, tree, chi, ops, whiches, tol_c=1e-12, tol_s=1e-10, min_gap=1e-8):
     """Compare every op in `ops` (increasing) for instances ids[w], w in whiches.
 
-    Returns a summary dict: ops checked, compressions skipped as ambiguous
+    Returns a summary dict: ops checked, S ops that did not fire (shared bond
+    size <= chi, as Algorithm 1 skips them), compressions skipped as ambiguous
     (relative cut gap below min_gap, where several truncations are correct),
     and the largest deviations seen.  A compression whose cut gap g is small
     but above min_gap is allowed a deviation of 1e-15 / g when that exceeds
     tol_s: the kept subspace itself is only determined to about that.
     """
-    out = {"c_ops": 0, "s_ops": 0, "ambiguous": 0, "max_c": 0.0, "max_s": 0.0}
+    out = {"c_ops": 0, "s_ops": 0, "ambiguous": 0, "noop": 0, "max_c": 0.0, "max_s": 0.0}
     for r in ops:
         op = tree.ops[r]
         # every instance's inputs first (state after op r - 1), then the outputs:
@@ -70,6 +71,7 @@ def walk(ctx, ids, tree, chi, ops, whiches, tol_c=1e-12, tol_s=1e-10, min_gap=1e
                 aj, baj = ctx.debug_tensor(ids, w, chi, r, op[2])
                 new = [b for b in bai if b not in bi]
                 if not new:          # D_AB <= chi: the op did not compress
+                    out["noop"] += 1
                     continue
                 res = approx.compress_pair(ti, bi, tj, bj, chi, new[0])
                 assert res is not None
