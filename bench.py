@@ -74,6 +74,7 @@ class Normal32:
 
     def __init__(self, args):
         self.N = args.batch or self.N
+        self.L = getattr(args, "L", 0) or self.L
 
     def describe(self):
         return (f"{self.L}x{self.L} open square lattice, D={self.D}, entries i.i.d. Normal(0.2,1), "
@@ -371,7 +372,8 @@ def run_ours(args):
     build.build()
     wl = WORKLOADS[args.workload](args)
     stream = torch.cuda.current_stream(device)
-    ctx = Context(local, stream=stream)
+    cache = os.path.join(tempfile.gettempdir(), f"tn_tune_{wl.name}_gpu{local}.txt")
+    ctx = Context(local, stream=stream, tuner_cache=cache if args.tune else None)
     nets = wl.nets(rank)
     tree = wl.tree()
     net_ids = [ctx.load_network(x) for x in nets]
@@ -386,6 +388,29 @@ def run_ours(args):
 
     def step():
         return ctx.contract(ids, wl.CHI, args.prec)
+
+    def eager_pass_ms():
+        ctx.set_graph_mode(False)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ctx.set_graph_mode(True)
+        return a.elapsed_time(b)
+
+    # launch-shape autotuner: one eager pass with the built-in rules, the tuning
+    # (cached in a file for later runs), one eager pass with the tuned shapes
+    tuner = None
+    if args.tune:
+        untuned = eager_pass_ms()
+        t0 = time.perf_counter()
+        shapes = ctx.autotune(ids, wl.CHI, args.prec)
+        tune_s = time.perf_counter() - t0
+        tuned = eager_pass_ms()
+        tuner = {"untuned_pass_ms": untuned, "tuned_pass_ms": tuned, "gain": untuned / tuned,
+                 "shapes_tuned": shapes, "tune_s": tune_s, "cache": cache,
+                 "how": "one eager pass each (CUDA events), before the warm-up; the timed steps use the tuned shapes"}
 
     # warm-up: the first pass runs eagerly, the second captures the schedule as a
     # CUDA graph, later passes replay it
@@ -507,6 +532,7 @@ def run_ours(args):
                          max(1, dict((a, b) for a, b, _ in fam).get("jacobi_" + prec_, 0) * nb), 3)
             for prec_ in ("f32", "f64")},
         "profiled_pass_ms": prof_ms,
+        "tuner": tuner,
         "graph": graph,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
@@ -592,9 +618,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="normal32", choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=0, help="instances per GPU per step (0: the workload's default)")
+    ap.add_argument("--L", type=int, default=0, help="normal32: lattice side (a smaller case for profiling)")
     ap.add_argument("--prec", default="f64", choices=["f64", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end leg (at most --steps)")
     ap.add_argument("--plain-calls", type=int, default=3, help="timed calls of the unbatched FP64 form")
+    ap.add_argument("--tune", type=int, default=1, help="1: run the launch-shape autotuner before the warm-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the unbatched and mixed-form legs")
     ap.add_argument("--gemm-check", type=int, default=0, metavar="G",
