@@ -373,7 +373,7 @@ def run_ours(args):
     wl = WORKLOADS[args.workload](args)
     stream = torch.cuda.current_stream(device)
     cache = os.path.join(tempfile.gettempdir(), f"tn_tune_{wl.name}_gpu{local}.txt")
-    ctx = Context(local, stream=stream, tuner_cache=cache if args.tune else None)
+    ctx = Context(local, stream=stream, tuner_cache=cache if args.tune else None, split_batches=args.split)
     nets = wl.nets(rank)
     tree = wl.tree()
     net_ids = [ctx.load_network(x) for x in nets]
@@ -515,7 +515,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.prec == "f64" else args.prec, "data": "synthetic",
         "config": {"workload": wl.describe(), "instances_per_gpu": nb, "chi": wl.CHI, "prec": args.prec,
-                   "tree": "boundary rows",
+                   "tree": "boundary rows", "split_batches": args.split,
                    "l2": "working set %.0f MB per GPU > 129 MB L2 (no flush needed)" % (stats["peak_bytes"] * nb / 1e6)},
         "contraction_tflops": gflop_step / (ms_max / 1e3) / 1e3,
         "e2e": {"value": world * nb / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -623,6 +623,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end leg (at most --steps)")
     ap.add_argument("--plain-calls", type=int, default=3, help="timed calls of the unbatched FP64 form")
     ap.add_argument("--tune", type=int, default=1, help="1: run the launch-shape autotuner before the warm-up")
+    ap.add_argument("--split", type=int, default=1, help="run each batch as this many concurrent sub-batches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the unbatched and mixed-form legs")
     ap.add_argument("--gemm-check", type=int, default=0, metavar="G",

@@ -135,7 +135,14 @@ typedef struct {
  *                      several groups (different structures or trees) runs
  *                      the groups one after the other; 0 (default): as
  *                      concurrent branches of one pass (see
- *                      tn_contract_approx).  Results are identical. */
+ *                      tn_contract_approx).  Results are identical.
+ *   split_batches      k >= 2: each batch of instances sharing a tree runs
+ *                      as k concurrent sub-batches (branches of one pass, as
+ *                      for several groups), so that one sub-batch's kernels
+ *                      fill the SMs another leaves idle; 0 or 1 (default):
+ *                      one batch.  Results may differ in the last bits from
+ *                      the unsplit batch (launch shapes depend on the batch
+ *                      size).  Requires sequential_groups = 0. */
 typedef struct {
   int32_t struct_size;
   int32_t graph_mode;
@@ -146,7 +153,7 @@ typedef struct {
   int32_t reserved;
   const char* tuner_cache;
   int32_t sequential_groups;
-  int32_t reserved2;
+  int32_t split_batches;
 } tn_options;
 
 /* Default options (struct_size = sizeof(tn_options)). */

@@ -147,6 +147,7 @@ struct tn_ctx {
   } multi;
   int64_t concurrent_runs = 0;
   int concurrent_groups = 1;  // run groups with different trees as concurrent branches
+  int split_batches = 1;      // > 1: each group's batch runs as this many concurrent sub-batches
   // tn_debug_tensor: where the last partial run stopped (its plan, members and
   // buffer generation), so that a later call with a later stop continues from there
   uint64_t dbg_serial = 0, dbg_gen = 0;
@@ -832,7 +833,7 @@ int tn_create(tn_ctx** out, int device, const tn_options* opt) {
   }
   if (o.graph_mode < 0 || o.graph_mode > 1 || o.grad_segments < 0 || o.debug_max_sweeps < 0 ||
       !(o.tape_budget_bytes >= 0.0) || o.debug_tc_give_up < 0 || o.debug_tc_give_up > 1 ||
-      o.sequential_groups < 0 || o.sequential_groups > 1)
+      o.sequential_groups < 0 || o.sequential_groups > 1 || o.split_batches < 0 || o.split_batches > 64)
     return TN_EINVAL;
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TN_ECUDA;
@@ -845,6 +846,7 @@ int tn_create(tn_ctx** out, int device, const tn_options* opt) {
   c->opt_max_sweeps = o.debug_max_sweeps;
   c->opt_tc_give_up = o.debug_tc_give_up != 0;
   c->concurrent_groups = o.sequential_groups ? 0 : 1;
+  c->split_batches = o.split_batches > 0 ? o.split_batches : 1;
   if (o.tuner_cache && *o.tuner_cache) {
     c->tuner_cache = o.tuner_cache;
     DeviceGuard g(device);
@@ -1068,7 +1070,26 @@ int tn_contract_approx(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int 
   bool distinct = true;
   for (size_t a = 0; a < plans.size(); ++a)
     for (size_t b = a + 1; b < plans.size(); ++b) distinct = distinct && plans[a] != plans[b];
-  if (groups.size() >= 2 && !c->profile && c->concurrent_groups && distinct) {
+  // tn_options.split_batches: each group's batch runs as that many concurrent
+  // sub-batches (they share the group's plan, which is read-only)
+  if (distinct && c->split_batches > 1 && !c->profile && c->concurrent_groups) {
+    std::vector<std::vector<int>> g2, p2;
+    std::vector<const tnp::Plan*> pl2;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+      const int nb = (int)groups[gi].size();
+      const int parts = std::min(c->split_batches, nb);
+      for (int q = 0; q < parts; ++q) {
+        const int lo = nb * q / parts, hi = nb * (q + 1) / parts;
+        g2.emplace_back(groups[gi].begin() + lo, groups[gi].begin() + hi);
+        p2.emplace_back(poss[gi].begin() + lo, poss[gi].begin() + hi);
+        pl2.push_back(plans[gi]);
+      }
+    }
+    groups.swap(g2);
+    poss.swap(p2);
+    plans.swap(pl2);
+  }
+  if (groups.size() >= 2 && !c->profile && c->concurrent_groups && (distinct || c->split_batches > 1)) {
     std::vector<std::vector<double>> lg;
     std::vector<std::vector<int>> sg;
     const int rc = run_groups_concurrent(c, plans, groups, &lg, &sg);

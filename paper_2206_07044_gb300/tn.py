@@ -50,7 +50,7 @@ class Options(C.Structure):
     _fields_ = [("struct_size", C.c_int32), ("graph_mode", C.c_int32), ("grad_segments", C.c_int32),
                 ("debug_max_sweeps", C.c_int32), ("tape_budget_bytes", C.c_double),
                 ("debug_tc_give_up", C.c_int32), ("reserved", C.c_int32), ("tuner_cache", C.c_char_p),
-                ("sequential_groups", C.c_int32), ("reserved2", C.c_int32)]
+                ("sequential_groups", C.c_int32), ("split_batches", C.c_int32)]
 
 
 # every symbol include/tn.h declares, with its ctypes signature
@@ -157,12 +157,12 @@ class Context:
     def __init__(self, device: int = 0, stream=None, **options):
         """options: any field of tn_options (graph_mode, grad_segments,
         tape_budget_bytes, debug_max_sweeps, debug_tc_give_up, tuner_cache,
-        sequential_groups); the rest keep their defaults."""
+        sequential_groups, split_batches); the rest keep their defaults."""
         self._L = lib()
         opt = Options()
         self._L.tn_options_default(C.byref(opt))
         for k, v in options.items():
-            if k in ("struct_size", "reserved", "reserved2") or k not in dict(Options._fields_):
+            if k in ("struct_size", "reserved") or k not in dict(Options._fields_):
                 raise TypeError(f"unknown tn_options field {k!r}")
             if k == "tuner_cache":
                 self._tuner_cache = v.encode() if isinstance(v, str) else v

@@ -71,3 +71,25 @@ def test_uneven_graphs_match_oracle_and_sequential_bitwise():
         assert abs(l - want.logabs) <= 1e-10 * abs(want.logabs), (l, want.logabs)
         checked += 1
     assert checked >= 4
+
+
+def test_split_batch_runs_as_concurrent_sub_batches():
+    """tn_options.split_batches = 3: a batch of six instances sharing one tree runs as three
+    concurrent sub-batches; the values agree with the unsplit batch and the oracle (16x16
+    D=4 chi=64, a well-conditioned case), and the captured pass replays bit for bit."""
+    n, e = nw.square_lattice(16, 16)
+    tree = tr.boundary_rows(16, 16)
+    nets = [nw.random_network(n, e, 4, seed=200 + s) for s in range(6)]
+    one = _ctx()
+    lz1, _ = one.contract([one.load_tree(one.load_network(x), tree) for x in nets], 64)
+    one.close()
+    c = _ctx(split_batches=3)
+    ids = [c.load_tree(c.load_network(x), tree) for x in nets]
+    runs = [c.contract(ids, 64)[0] for _ in range(3)]
+    c.close()
+    assert all(np.array_equal(runs[0], r) for r in runs[1:])
+    for s in (0, 5):
+        want = approx.contract(nets[s], tree, 64)
+        assert min(d[2] for d in want.diag) > 1e-8
+        assert abs(runs[0][s] - want.logabs) <= 1e-10 * abs(want.logabs)
+    assert np.all(np.abs(runs[0] - lz1) <= 1e-10 * np.abs(lz1))
