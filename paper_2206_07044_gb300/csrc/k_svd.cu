@@ -87,6 +87,8 @@ struct JacArgs {
   T tol2, sig_tol2; // (set in the kernel) tol^2, sig_tol^2
   T noise2;         // (set in the kernel) (64 eps |G|_F)^2: the matrix's rounding floor for an off-diagonal
   unsigned long long* sweep_ctr;  // optional: total sweeps run, summed over matrices
+  const int* active;  // optional, n ints per matrix (stride act_bs): convergence is judged on pairs
+  int64_t act_bs;     //   with at least one active column (every pair is still rotated)
 };
 
 // Squared Frobenius norm of G.  Each CTA writes its partial sum to its own
@@ -223,6 +225,8 @@ __global__ void __launch_bounds__(kMaxJacThreads) block_jacobi_kernel(JacArgs<T>
   T* Vs = Gs + (size_t)2 * b * m;                          // 2b columns of length n (if V)
   T* nrm = Vs + (has_v ? (size_t)2 * b * n : 0);           // 2b cached squared norms
   int* col = reinterpret_cast<int*>(nrm + 2 * b);          // global column of each slot (-1 = pad)
+  int* act = col + 2 * b;                                  // 1 if the slot's column is active
+  const int* active = p.active ? p.active + (int64_t)bidx * p.act_bs : nullptr;
   __shared__ int sig_rot_s;
 
   if (has_v && p.init_v) {
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(kMaxJacThreads) block_jacobi_kernel(JacArgs<T>
       for (int s = threadIdx.x; s < 2 * b; s += blockDim.x) {
         const int gc = (s < b ? pa : pb) * b + (s % b);
         col[s] = gc < n ? gc : -1;
+        act[s] = (gc < n && (!active || active[gc])) ? 1 : 0;
       }
       __syncthreads();
       for (int s = warp; s < 2 * b; s += nwarps) {
@@ -280,7 +285,8 @@ __global__ void __launch_bounds__(kMaxJacThreads) block_jacobi_kernel(JacArgs<T>
             if (x > y) { int t = x; x = y; y = t; }
             T al = nrm[x], be = nrm[y];
             if (jacobi_pair(Gs + (size_t)x * m, Gs + (size_t)y * m, has_v ? Vs + (size_t)x * n : nullptr,
-                            has_v ? Vs + (size_t)y * n : nullptr, m, n, al, be, p, lane))
+                            has_v ? Vs + (size_t)y * n : nullptr, m, n, al, be, p, lane) &&
+                (act[x] | act[y]))
               sig_rot += (lane == 0);
             if (lane == 0) { nrm[x] = al; nrm[y] = be; }
           }
@@ -294,7 +300,8 @@ __global__ void __launch_bounds__(kMaxJacThreads) block_jacobi_kernel(JacArgs<T>
             if (col[x] < 0 || col[y] < 0) continue;
             T al = nrm[x], be = nrm[y];
             if (jacobi_pair(Gs + (size_t)x * m, Gs + (size_t)y * m, has_v ? Vs + (size_t)x * n : nullptr,
-                            has_v ? Vs + (size_t)y * n : nullptr, m, n, al, be, p, lane))
+                            has_v ? Vs + (size_t)y * n : nullptr, m, n, al, be, p, lane) &&
+                (act[x] | act[y]))
               sig_rot += (lane == 0);
             if (lane == 0) { nrm[x] = al; nrm[y] = be; }
           }
@@ -395,8 +402,9 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
         al = warp_sum(al);
         be = warp_sum(be);
         __syncwarp();
+        const bool counted = !p.active || p.active[(int64_t)bidx * p.act_bs + i] | p.active[(int64_t)bidx * p.act_bs + j];
         if (jacobi_pair<T, true>(gi, gj, V ? V + (int64_t)i * n : nullptr, V ? V + (int64_t)j * n : nullptr, m, n,
-                                 al, be, p, lane))
+                                 al, be, p, lane) && counted)
           sig_rot += (lane == 0);
       }
       cl.sync();
@@ -426,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
 template <typename T>
 size_t block_smem(int m, int n, int P, bool has_v) {
   const int b = (n + 2 * P - 1) / (2 * P);
-  return (size_t)2 * b * (m + (has_v ? n : 0)) * sizeof(T) + (size_t)2 * b * (sizeof(T) + sizeof(int)) + 16;
+  return (size_t)2 * b * (m + (has_v ? n : 0)) * sizeof(T) + (size_t)2 * b * (sizeof(T) + 2 * sizeof(int)) + 16;
 }
 
 constexpr size_t kSmemCap = 200 * 1024;
@@ -562,6 +570,63 @@ __global__ void select_scale_kernel(int m, int n, int k, const double* Gall, int
   }
 }
 
+// Active columns of the FP64 polish (one CTA per matrix).  G (m x n, column
+// major) is the FP64 product M V with V the re-orthonormalised FP32 basis, so
+// its column norms are the singular values to FP32 accuracy.  Only the k
+// largest enter the truncation (Eq. "svd"), so the polish judges convergence
+// on the pairs that touch them: it still rotates every pair (skipping pairs
+// would let the coupling of two skipped columns flow back into kept ones), but
+// a pair of two inactive columns no longer keeps the sweep loop alive.  Column
+// i is active when its rank is below k + 16 or its norm is at least half the
+// k-th largest.  When the k-th norm is within 1e-4 of |G|_F (where the FP32
+// ordering is not trusted) or k + 16 >= n, every column is active.
+__global__ void mark_active_kernel(int m, int n, int k, const double* Gall, int64_t g_bs, int* act_all,
+                                   int64_t act_bs) {
+  const int b = blockIdx.x;
+  const double* G = Gall + (int64_t)b * g_bs;
+  int* act = act_all + (int64_t)b * act_bs;
+  extern __shared__ double nrm2[];
+  __shared__ double fro2_s, kth_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int c = warp; c < n; c += nwarps) {
+    double s2 = 0.0;
+    for (int r = lane; r < m; r += 32) {
+      const double x = G[(int64_t)c * m + r];
+      s2 = fma(x, x, s2);
+    }
+    s2 = warp_sum(s2);
+    if (lane == 0) nrm2[c] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int c = 0; c < n; ++c) f += nrm2[c];
+    fro2_s = f;
+    kth_s = -1.0;
+  }
+  __syncthreads();
+  // the k-th largest: the column of rank k - 1 (ties by index)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double si = nrm2[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) r += (nrm2[j] > si) || (nrm2[j] == si && j < i);
+    if (r == k - 1) kth_s = si;
+    act[i] = r;  // rank, replaced by the flag below
+  }
+  __syncthreads();
+  const double kth = kth_s;
+  const bool all = (k + 16 >= n) || !(kth >= 1e-8 * fro2_s);
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    act[i] = (all || act[i] < k + 16 || nrm2[i] >= 0.25 * kth) ? 1 : 0;
+}
+
+constexpr int kMarkMaxN = 6144;  // n doubles of shared memory within the 48 KB default
+
+__global__ void all_active_kernel(int n, int* act_all, int64_t act_bs) {
+  int* act = act_all + (int64_t)blockIdx.x * act_bs;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) act[i] = 1;
+}
+
 __global__ void to_f32_kernel(const double* __restrict__ x, int64_t n, int64_t xbs, float* __restrict__ y,
                               int64_t ybs) {
   const int b = blockIdx.y;
@@ -590,19 +655,20 @@ cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64
                            DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr, int max_sweeps) {
   // a preconditioner: running out of sweeps is not an error (the FP64 stage decides)
   JacArgs<float> a{m, n, G, g_bs, V, v_bs, nullptr, 0, ws, nullptr, 1, max_sweeps > 0 ? max_sweeps : 60,
-                   4.0f * (float)m * FLT_EPSILON, 3e-4f, 1e-6f, 0.0f, 0.0f, 0.0f, 0.0f, sweep_ctr};
+                   4.0f * (float)m * FLT_EPSILON, 3e-4f, 1e-6f, 0.0f, 0.0f, 0.0f, 0.0f, sweep_ctr, nullptr, 0};
   return launch_jacobi(a, batch, s);
 }
 
 cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int64_t v_bs, double* sig,
                            int64_t sig_bs, int* ws, DevState st, int init_v, int batch, cudaStream_t s,
-                           unsigned long long* sweep_ctr, double sig_tol, int max_sweeps) {
+                           unsigned long long* sweep_ctr, double sig_tol, int max_sweeps, const int* active,
+                           int64_t act_bs) {
   // rotate down to sqrt(m) eps (the cut's subspace error is that over the gap);
   // convergence is judged by the looser sig_tol, so rounding-level rotations
   // never keep the sweep loop alive
   const double rt = sqrt((double)(m > 16 ? m : 16));
   JacArgs<double> a{m, n, G, g_bs, V, v_bs, sig, sig_bs, ws, st.status, init_v, max_sweeps > 0 ? max_sweeps : 60,
-                    rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, 0.0, 0.0, 0.0, sweep_ctr};
+                    rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, 0.0, 0.0, 0.0, sweep_ctr, active, act_bs};
   return launch_jacobi(a, batch, s);
 }
 
@@ -614,6 +680,18 @@ cudaError_t select_scale_f64(int m, int n, int k, const double* G, int64_t g_bs,
   if (n > 8192 || ldl < m || ldr < n || (!V && !K3)) return cudaErrorInvalidValue;
   select_scale_kernel<<<batch, 256, (size_t)n * sizeof(int), s>>>(m, n, k, G, g_bs, V, v_bs, sig, sig_bs, L,
                                                                    l_bs, ldl, R, r_bs, ldr, K3, k3_bs);
+  return cudaGetLastError();
+}
+
+cudaError_t mark_active_f64(int m, int n, int k, const double* G, int64_t g_bs, int* act, int64_t act_bs, int batch,
+                            cudaStream_t s) {
+  if (batch <= 0 || n <= 0) return cudaSuccess;
+  if (k < 1 || batch > 65535) return cudaErrorInvalidValue;
+  if (n > kMarkMaxN) {  // too wide for the shared-memory ranking: every column counts
+    all_active_kernel<<<batch, 256, 0, s>>>(n, act, act_bs);
+    return cudaGetLastError();
+  }
+  mark_active_kernel<<<batch, 256, (size_t)n * sizeof(double), s>>>(m, n, k, G, g_bs, act, act_bs);
   return cudaGetLastError();
 }
 

@@ -75,7 +75,8 @@ struct GraphRec {
 
 const char* kFamily[] = {"permute", "gemm_f64",   "qr_f64",     "jacobi_f64",  "select_scale", "rescale",
                          "finalize", "to_f32",     "jacobi_f32", "to_f64",      "copy",         "apply_q_f64",
-                         "gemm_tc",  "scale_pow2", "final_grad", "svd_factors", "svd_adj_core", "copy2d"};
+                         "gemm_tc",  "scale_pow2", "final_grad", "svd_factors", "svd_adj_core", "copy2d",
+                         "mark_active"};
 static_assert(sizeof(kFamily) / sizeof(kFamily[0]) == tnp::kNumStepKinds, "one family name per step kind");
 constexpr int kNumFamily = tnp::kNumStepKinds;
 

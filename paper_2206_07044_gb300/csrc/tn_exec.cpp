@@ -22,7 +22,9 @@ cudaError_t exec_step(const tnp::Step& stp, const ExecEnv& env, cudaStream_t s) 
     case tnp::ST_JACOBI:
       return tnk::jacobi_svd_f64(stp.m, stp.n, ptr(stp.C), stp.C.bs, stp.no_v ? nullptr : ptr(stp.aux1),
                                  stp.aux1.bs, ptr(stp.aux2), stp.aux2.bs, env.jac_ws, env.ds, stp.init_v, batch, s,
-                                 env.sweeps64, stp.jac_tol, env.jac_max_sweeps);
+                                 env.sweeps64, stp.jac_tol, env.jac_max_sweeps,
+                                 stp.work.bs > 0 ? reinterpret_cast<const int*>(ptr(stp.work)) : nullptr,
+                                 2 * stp.work.bs);
     case tnp::ST_TO_F32:
       return tnk::convert_f64_to_f32(ptr(stp.src), stp.count, stp.src.bs, reinterpret_cast<float*>(ptr(stp.dst)),
                                      stp.fbs_dst, batch, s);
@@ -68,6 +70,9 @@ cudaError_t exec_step(const tnp::Step& stp, const ExecEnv& env, cudaStream_t s) 
                                        stp.work.bs, ptr(stp.C), stp.C.bs, batch, s);
     case tnp::ST_COPY2D:
       return tnk::copy2d_f64(stp.m, stp.n, cview(stp.A), wview(stp.C), batch, s);
+    case tnp::ST_MARK_ACTIVE:
+      return tnk::mark_active_f64(stp.m, stp.n, stp.k, ptr(stp.C), stp.C.bs, reinterpret_cast<int*>(ptr(stp.out1)),
+                                  2 * stp.out1.bs, batch, s);
     default:
       return cudaErrorInvalidValue;
   }

@@ -46,11 +46,19 @@ cudaError_t qr_r_f64(int m, int n, View A, double* work, int64_t work_bs, ViewW 
 // sigma_i (unsorted).  ws: 64 ints per batch of scratch.  Sets st.status[b] = -9
 // if the bounded sweep loop ran out.
 // sweep_ctr (optional, device): the sweeps run are added to it.  max_sweeps
-// caps the sweep loop (0: 60 sweeps).
+// caps the sweep loop (0: 60 sweeps).  active (optional): see mark_active_f64.
 cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int64_t v_bs,
                            double* sig, int64_t sig_bs, int* ws, DevState st, int init_v,
                            int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr,
-                           double sig_tol = 1e-8, int max_sweeps = 0);
+                           double sig_tol = 1e-8, int max_sweeps = 0, const int* active = nullptr,
+                           int64_t act_bs = 0);
+// Active columns of the FP64 polish (act: n ints per matrix, stride act_bs):
+// 1 for the columns of G (m x n column-major) ranked below k + 16 by norm or
+// within a factor 2 of the k-th largest norm, 0 for the rest; all 1 when the
+// k-th norm is below 1e-4 |G|_F or k + 16 >= n.  The polish rotates every
+// pair but judges convergence only on pairs with an active column.
+cudaError_t mark_active_f64(int m, int n, int k, const double* G, int64_t g_bs, int* act, int64_t act_bs, int batch,
+                            cudaStream_t s);
 // The FP32 preconditioning pass (V = I first); never sets a status.
 cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64_t v_bs, int* ws,
                            DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr = nullptr,

@@ -1057,11 +1057,28 @@ struct Builder {
     G.rs = 1;
     G.cs = Jm;
     gemm((int)Jm, (int)Jn, (int)Jn, M0c, Vc, G, 1.0, 0.0, true);
-    // 3. FP64 Jacobi from V: converges quadratically to the FP64 SVD
+    // 3. FP64 Jacobi from V: converges quadratically to the FP64 SVD.  Without
+    // V (the forward pass) only the kk kept directions are used: the polish
+    // still rotates every pair, but judges convergence on the pairs touching
+    // the kept columns (mark_active_f64)
     PView sig = tmp(Jn);
+    PView act;
+    if (!keep_v) {
+      act = tmp((Jn + 1) / 2);
+      Step mk;
+      mk.kind = ST_MARK_ACTIVE;
+      mk.m = (int)Jm;
+      mk.n = (int)Jn;
+      mk.k = (int)kk;
+      mk.C = G;
+      mk.out1 = act;
+      mk.bytes = 8.0 * (double)Jm * Jn;
+      add(mk);
+    }
     {
       Step st;
       st.kind = ST_JACOBI;
+      st.work = act;
       st.m = (int)Jm;
       st.n = (int)Jn;
       st.C = G;

@@ -45,8 +45,9 @@ enum StepKind : int {
                         //   -> out1 = U, out2 = W, work = s, A = Us, B = Ws
   ST_SVD_ADJ_CORE = 16, // C (n x n) from A = P, B = Q (n x k), work = s
   ST_COPY2D = 17,       // C view <- A view (m x n)
+  ST_MARK_ACTIVE = 18,  // active columns of the FP64 polish: C = G (m x n), k kept -> out1 (n ints per instance)
 };
-constexpr int kNumStepKinds = 18;
+constexpr int kNumStepKinds = 19;
 
 struct Step {
   int kind = 0;

@@ -23,7 +23,7 @@ import numpy as np
 BUF_ARENA, BUF_INPUT, BUF_GIN = 0, 1, 2
 (ST_PERMUTE, ST_GEMM, ST_QR, ST_JACOBI, ST_SELECT, ST_RESCALE, ST_FINAL, ST_TO_F32, ST_JACOBI32, ST_TO_F64,
  ST_COPY, ST_APPLYQ, ST_GEMM_TC, ST_SCALE_POW2, ST_FINAL_GRAD, ST_SVD_FACTORS, ST_SVD_ADJ_CORE,
- ST_COPY2D) = range(18)
+ ST_COPY2D, ST_MARK_ACTIVE) = range(19)
 
 
 class Emulator:
@@ -183,6 +183,11 @@ class Emulator:
                 varr[vix] = V @ W
             sarr, six = self.colmajor(st["aux2"], b, n, 1)
             sarr[six] = np.linalg.norm(G2, axis=0)[:, None]
+
+    def k18(self, st):  # active columns of the FP64 polish
+        # Nothing to replay: they only decide when the polish's sweep loop may
+        # stop, and the emulated polish (k3) is an exact SVD of the core.
+        pass
 
     def k7(self, st):  # FP64 -> FP32
         n = st["count"]
