@@ -131,6 +131,7 @@ class Ising64:
 
     def __init__(self, args):
         self.B = args.batch or 32
+        self.form_list = [f for f in (getattr(args, "forms", "") or "f64,tf32x3,tf32,bf16").split(",") if f]
         with open(os.path.join(ROOT, "tests", "golden", "ising64_chi128.json")) as f:
             self.gold = json.load(f)["entries"]
 
@@ -173,7 +174,7 @@ class Ising64:
                       "max(1e-6, 4 x the oracle's rounding spread there)", "gate_rel_err": GATE,
                "band": {"%.4f" % e["beta"]: max(GATE, 4 * e["spread_rel"]) for e in self.gold}}
         ng = len(self.gold)
-        for prec in ("f64", "tf32x3", "tf32", "bf16"):
+        for prec in self.form_list:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             lz, _ = ctx.contract(ids, self.CHI, prec)
@@ -504,7 +505,7 @@ def run_ours(args):
     gflop_step = (stats["gemm_flops"] + stats["qr_flops"] + stats["svd_flops"]) * nb * world / 1e9
     gated = None
     if forms:
-        ok = [p for p in ("f64", "tf32x3", "tf32", "bf16") if forms.get(p, {}).get("meets_gate")]
+        ok = [p for p in ("f64", "tf32x3", "tf32", "bf16") if isinstance(forms.get(p), dict) and forms[p].get("meets_gate")]
         speed = {p: forms[p].get("evals_per_s", value if p == args.prec else None) for p in ok}
         speed = {p: v for p, v in speed.items() if v}
         if speed:
@@ -622,6 +623,7 @@ def main():
     ap.add_argument("--L", type=int, default=0, help="normal32: lattice side (a smaller case for profiling)")
     ap.add_argument("--prec", default="f64", choices=["f64", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end leg (at most --steps)")
+    ap.add_argument("--forms", default="", help="ising64: comma-separated forms to time against the stored values")
     ap.add_argument("--plain-calls", type=int, default=3, help="timed calls of the unbatched FP64 form")
     ap.add_argument("--tune", type=int, default=1, help="1: run the launch-shape autotuner before the warm-up")
     ap.add_argument("--split", type=int, default=1, help="run each batch as this many concurrent sub-batches")
