@@ -95,6 +95,31 @@ class Normal32:
         n, edges = nw.square_lattice(self.L, self.L)
         return nw.random_network(n, edges, self.D, seed=idx)
 
+    def trees(self, ctx, torch, net_ids, nets):
+        """Tree builders on the benchmark batch (Algorithm 3's loop closed on the GPU): the
+        boundary rows, the hyper-searched Span tree and the Greedy tree with the SI's max
+        input reduction; per tree the traced cost C (the SI's units) and one eager FP64 pass."""
+        from tn_inputs import trees as tr
+        out = {}
+        b = nets[0]
+        for name, tree in (("boundary rows", tr.boundary_rows(self.L, self.L)),
+                           ("span (hyper-searched, late)", tr.span(b.bonds, b.bond_dims, **tr.span_square_params())),
+                           ("greedy (SI max reduction)", tr.greedy(b.bonds, b.bond_dims, self.CHI,
+                                                                    **tr.greedy_front_params(self.CHI)))):
+            cost = tr.trace_cost(b.bonds, b.bond_dims, tree, self.CHI)
+            ids = [ctx.load_tree(nid, tree) for nid in net_ids]
+            ctx.set_graph_mode(False)
+            ctx.contract(ids, self.CHI)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lz, _ = ctx.contract(ids, self.CHI)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+            ctx.set_graph_mode(True)
+            out[name] = {"traced_cost": cost["total"], "traced_peak_elements": cost["peak"], "pass_ms": ms,
+                         "evals_per_s": len(ids) / (ms / 1e3), "logabsz_instance0": float(lz[0])}
+        return out
+
     def cpu_rows(self):
         return 8
 
@@ -462,7 +487,7 @@ def run_ours(args):
 
     # the plain FP64 form: the same contraction, one instance per call (no batching),
     # timed over several calls after one untimed call
-    plain = forms = None
+    plain = forms = trees_leg = None
     if rank == 0 and not args.no_forms:
         ctx.contract(ids[:1], wl.CHI, "f64")
         torch.cuda.synchronize()
@@ -475,6 +500,7 @@ def run_ours(args):
         plain = {"value": 1.0 / plain_s, "unit": UNIT, "ms_per_eval": plain_s * 1e3, "calls": calls,
                  "how": "one instance per tn_contract_approx call, FP64, same workload"}
         forms = wl.forms(ctx, torch, ids)
+        trees_leg = wl.trees(ctx, torch, net_ids, nets) if hasattr(wl, "trees") and not args.no_trees else None
     fp64_peak = fp64_peak_tflops(torch, device) if rank == 0 else None
 
     if rank != 0:
@@ -535,6 +561,7 @@ def run_ours(args):
             for prec_ in ("f32", "f64")},
         "profiled_pass_ms": prof_ms,
         "tuner": tuner,
+        "trees": trees_leg,
         "graph": graph,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
@@ -628,6 +655,7 @@ def main():
     ap.add_argument("--tune", type=int, default=1, help="1: run the launch-shape autotuner before the warm-up")
     ap.add_argument("--split", type=int, default=1, help="run each batch as this many concurrent sub-batches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-trees", action="store_true", help="skip the tree-builder leg")
     ap.add_argument("--no-forms", action="store_true", help="skip the unbatched and mixed-form legs")
     ap.add_argument("--gemm-check", type=int, default=0, metavar="G",
                     help="instead of the benchmark: throughput of each GEMM form on a (G^2)^3 contraction")

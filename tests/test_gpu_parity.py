@@ -111,6 +111,20 @@ def test_dimers_small_graph_exact_count(ctx):
     assert abs(math.exp(got) - exact.perfect_matchings(n, edges)) < 1e-8 * math.exp(got)
 
 
+@pytest.mark.parametrize("builder", ["span", "greedy"])
+def test_searched_trees_on_16x16_d4_chi64(ctx, builder):
+    """The hyper-searched Span tree (late compression) and the Greedy tree with the SI's
+    max input reduction on the benchmark's distribution at 16x16, against the oracle."""
+    n, edges = nw.square_lattice(16, 16)
+    net = nw.random_network(n, edges, 4, seed=1)
+    if builder == "span":
+        t = tr.span(net.bonds, net.bond_dims, **tr.span_square_params())
+    else:
+        t = tr.greedy(net.bonds, net.bond_dims, 64, **tr.greedy_front_params(64))
+    got, want = check(ctx, net, t, 64)
+    assert want.compressions > 50
+
+
 def test_cdl_exact_at_chi_4(ctx):
     net = nw.cdl_network(6, 6, 2)
     got, _ = gpu_run(ctx, net, tr.boundary_rows(6, 6), 4)

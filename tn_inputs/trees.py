@@ -427,6 +427,17 @@ def greedy_front_params(chi: int) -> Dict[str, object]:
     return dict(w_new=1.0, w_old=0.2, w_inputs=-0.85, inputs_mode="max", chi_greedy=max(1, chi // 2))
 
 
+# Span parameters that hyper_search(builder="span", n_trials=24, seed=0) found on
+# the 32 x 32, D = 4, chi = 64 lattice: late compression from a peripheral
+# start, candidates by centrality, then connectivity, then distance (traced
+# cost 1.59e11 against 1.82e11 for boundary rows; 2.62e10 against 3.38e10 on
+# 16 x 16).
+def span_square_params() -> Dict[str, object]:
+    return dict(policy="late", start="peripheral", priority=("centrality", "connectivity", "distance", "ndim"),
+                signs={"distance": -1.0, "connectivity": 1.0, "ndim": 1.0, "centrality": 1.0},
+                temperature=0.0, seed=18)
+
+
 def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int,
            seed: int = 0, temperature: float = 0.0, w_new: float = 1.0, w_old: float = 0.0,
            w_inputs: float = -1.0, w_subgraph: float = 0.0, w_centrality: float = 0.0,
