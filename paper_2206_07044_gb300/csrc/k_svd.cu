@@ -5,12 +5,15 @@
 // GB300 runs FP32 58x faster than FP64 (measured 69.7 vs 1.19 TFLOP/s), so the
 // core SVD runs in two precisions:
 //   1. FP32 Jacobi on a float copy of the core, from V = I, until every pair's
-//      relative off-diagonal is below 3e-4 (the last sweep leaves ~1e-7);
+//      relative off-diagonal is below 3e-4 (pairs below 4 m eps32 are skipped
+//      on the way), then one finishing sweep that rotates every pair above
+//      16 eps32: it takes the off-diagonals from ~1e-4 to the FP32 rounding
+//      level, which saves the FP64 stage one of its sweeps;
 //   2. (host schedule) V is re-orthonormalised in FP64 by two Newton-Schulz
 //      steps V <- V (3 I - V^T V) / 2 (from ~1e-5 to below 1e-16) and
 //      G = M V is formed in FP64;
 //   3. FP64 Jacobi on that G, starting from V, which converges quadratically in
-//      2-3 sweeps to FP64 accuracy.
+//      about 2 sweeps to FP64 accuracy.
 // The FP64 result is the exact-arithmetic fixed point of step 3; step 1 only
 // supplies the starting basis.
 //
@@ -83,6 +86,7 @@ struct JacArgs {
   T tol;            // rotate iff |gamma| > tol * sqrt(alpha beta)
   T sig_tol;        // ... and the pair is not yet converged iff |gamma| > sig_tol * sqrt(alpha beta)
   T floor_rel;      // columns with |g| <= floor_rel * |G|_F are left alone
+  T fin_tol;        // > 0: after convergence, one more sweep rotating every pair above fin_tol
   T floor2;         // (set in the kernel) floor_rel^2 * |G|_F^2
   T tol2, sig_tol2; // (set in the kernel) tol^2, sig_tol^2
   T noise2;         // (set in the kernel) (64 eps |G|_F)^2: the matrix's rounding floor for an off-diagonal
@@ -236,9 +240,10 @@ __global__ void __launch_bounds__(kMaxJacThreads) block_jacobi_kernel(JacArgs<T>
   if (rank == 0 && threadIdx.x < 3) cnt[threadIdx.x] = 0;
   cl.sync();
 
-  bool converged = (n < 2);
+  bool converged = (n < 2), finishing = false;
   int sweeps_run = 0;
-  for (int sweep = 0; sweep < p.max_sweeps && !converged; ++sweep) {
+  const int sweep_cap = p.max_sweeps + (p.fin_tol > T(0) ? 1 : 0);
+  for (int sweep = 0; sweep < sweep_cap && !converged; ++sweep) {
     ++sweeps_run;
     if (rank == 0 && threadIdx.x == 0) cnt[(sweep + 1) % 3] = 0;
     if (threadIdx.x == 0) sig_rot_s = 0;
@@ -329,6 +334,13 @@ __global__ void __launch_bounds__(kMaxJacThreads) block_jacobi_kernel(JacArgs<T>
     if (threadIdx.x == 0 && sig_rot_s) atomicAdd(cnt + (sweep % 3), sig_rot_s);
     cl.sync();
     converged = (__ldcg(cnt + (sweep % 3)) == 0);
+    if (finishing) {
+      converged = true;
+    } else if (converged && p.fin_tol > T(0)) {
+      converged = false;
+      finishing = true;
+      p.tol2 = p.fin_tol * p.fin_tol;
+    }
   }
   if (!converged && p.status && rank == 0 && threadIdx.x == 0) atomicExch(p.status + bidx, -9);
   if (p.sweep_ctr && rank == 0 && threadIdx.x == 0) atomicAdd(p.sweep_ctr, (unsigned long long)sweeps_run);
@@ -379,9 +391,10 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
   }
   if (rank == 0 && threadIdx.x < 3) cnt[threadIdx.x] = 0;
   cl.sync();
-  bool converged = (n < 2);
+  bool converged = (n < 2), finishing = false;
   int sweeps_run = 0;
-  for (int sweep = 0; sweep < p.max_sweeps && !converged; ++sweep) {
+  const int sweep_cap = p.max_sweeps + (p.fin_tol > T(0) ? 1 : 0);
+  for (int sweep = 0; sweep < sweep_cap && !converged; ++sweep) {
     ++sweeps_run;
     if (rank == 0 && threadIdx.x == 0) cnt[(sweep + 1) % 3] = 0;
     int sig_rot = 0;
@@ -413,6 +426,13 @@ __global__ void __launch_bounds__(kThreads) pair_jacobi_kernel(JacArgs<T> p) {
     if (lane == 0 && sig_rot) atomicAdd(cnt + (sweep % 3), sig_rot);
     cl.sync();
     converged = (__ldcg(cnt + (sweep % 3)) == 0);
+    if (finishing) {
+      converged = true;
+    } else if (converged && p.fin_tol > T(0)) {
+      converged = false;
+      finishing = true;
+      p.tol2 = p.fin_tol * p.fin_tol;
+    }
   }
   if (!converged && p.status && rank == 0 && threadIdx.x == 0) atomicExch(p.status + bidx, -9);
   if (p.sweep_ctr && rank == 0 && threadIdx.x == 0) atomicAdd(p.sweep_ctr, (unsigned long long)sweeps_run);
@@ -655,7 +675,8 @@ cudaError_t jacobi_svd_f32(int m, int n, float* G, int64_t g_bs, float* V, int64
                            DevState st, int batch, cudaStream_t s, unsigned long long* sweep_ctr, int max_sweeps) {
   // a preconditioner: running out of sweeps is not an error (the FP64 stage decides)
   JacArgs<float> a{m, n, G, g_bs, V, v_bs, nullptr, 0, ws, nullptr, 1, max_sweeps > 0 ? max_sweeps : 60,
-                   4.0f * (float)m * FLT_EPSILON, 3e-4f, 1e-6f, 0.0f, 0.0f, 0.0f, 0.0f, sweep_ctr, nullptr, 0};
+                   4.0f * (float)m * FLT_EPSILON, 3e-4f, 1e-6f, 16.0f * FLT_EPSILON, 0.0f, 0.0f, 0.0f, 0.0f,
+                   sweep_ctr, nullptr, 0};
   return launch_jacobi(a, batch, s);
 }
 
@@ -668,7 +689,7 @@ cudaError_t jacobi_svd_f64(int m, int n, double* G, int64_t g_bs, double* V, int
   // never keep the sweep loop alive
   const double rt = sqrt((double)(m > 16 ? m : 16));
   JacArgs<double> a{m, n, G, g_bs, V, v_bs, sig, sig_bs, ws, st.status, init_v, max_sweeps > 0 ? max_sweeps : 60,
-                    rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, 0.0, 0.0, 0.0, sweep_ctr, active, act_bs};
+                    rt * DBL_EPSILON, sig_tol, 1e-14, 0.0, 0.0, 0.0, 0.0, 0.0, sweep_ctr, active, act_bs};
   return launch_jacobi(a, batch, s);
 }
 
