@@ -107,15 +107,20 @@ class Normal32:
                            ("greedy (SI max reduction)", tr.greedy(b.bonds, b.bond_dims, self.CHI,
                                                                     **tr.greedy_front_params(self.CHI)))):
             cost = tr.trace_cost(b.bonds, b.bond_dims, tree, self.CHI)
-            ids = [ctx.load_tree(nid, tree) for nid in net_ids]
-            ctx.set_graph_mode(False)
-            ctx.contract(ids, self.CHI)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            lz, _ = ctx.contract(ids, self.CHI)
-            torch.cuda.synchronize()
-            ms = (time.perf_counter() - t0) * 1e3
-            ctx.set_graph_mode(True)
+            try:
+                ids = [ctx.load_tree(nid, tree) for nid in net_ids]
+                ctx.set_graph_mode(False)
+                ctx.contract(ids, self.CHI)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lz, _ = ctx.contract(ids, self.CHI)
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t0) * 1e3
+            except RuntimeError as e:  # a tree whose plan does not fit is reported, not fatal
+                out[name] = {"traced_cost": cost["total"], "traced_peak_elements": cost["peak"], "error": str(e)}
+                continue
+            finally:
+                ctx.set_graph_mode(True)
             out[name] = {"traced_cost": cost["total"], "traced_peak_elements": cost["peak"], "pass_ms": ms,
                          "evals_per_s": len(ids) / (ms / 1e3), "logabsz_instance0": float(lz[0])}
         return out
