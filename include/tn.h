@@ -165,7 +165,7 @@ void tn_options_default(tn_options* opt);
  * (no such device). */
 int tn_create(tn_ctx** out, int device, const tn_options* opt);
 
-/* Autotuner of the launch shapes (the survey's tile autotuner): for the plan
+/* Autotuner of the launch shapes (tile and cluster sizes): for the plan
  * of the instances' groups at this chi and form, every distinct launch shape
  * of the QR, the FP32 and FP64 Jacobi passes (cluster size P of the
  * one-matrix-per-cluster kernels) and the GEMMs that carry 98% of the plan's
