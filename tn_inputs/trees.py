@@ -12,6 +12,13 @@ sweep or every seed of a random ensemble.  Generators:
 * ``greedy``: the Greedy builder of the SI (local score from the sizes before
   and after compression, input sizes, sub-graph sizes, centrality and a
   Gumbel noise term), simulated with chi_greedy.
+* ``span``: the Span builder (a spanning tree grown by Algorithm 2,
+  contracted leaves inwards).
+* ``agglom``: the Agglom builder of the SI (balanced communities from a graph
+  partitioner, Greedy inside each, compression between them, repeated on
+  the coarse network).
+* ``hyper_search``: random search over any builder's parameters scored by
+  the cost tracer (Algorithm 3).
 
 The shape simulation here only decides an order; it never touches tensor
 entries.  A compression of the bonds shared by A and B yields one bond of
@@ -438,6 +445,51 @@ def span_square_params() -> Dict[str, object]:
                 temperature=0.0, seed=18)
 
 
+def _greedy_loop(sim: "_Sim", members: set, chig: int, score, ops: List[tuple], nxt: int, on_contract=None) -> int:
+    """Contract adjacent pairs of the live tensors in ``members`` (updated in
+    place), lowest ``score(i, j)`` first, until no two members share a bond.
+    After each contraction C i j -> k, an S op with every neighbour of k
+    (ascending, members or not), simulated at chig: Algorithm 1's early
+    compression.  Stale heap entries are recognised by per-tensor versions,
+    bumped when a compression changes a tensor.  Returns the next free id."""
+    version: Dict[int, int] = {v: 0 for v in members}
+    heap: List[Tuple[float, int, int, int, int]] = []
+
+    def push_around(t: int) -> None:
+        for l in sim.groups(t):
+            if l in members:
+                a, b = (t, l) if t < l else (l, t)
+                heapq.heappush(heap, (score(a, b), a, b, version[a], version[b]))
+
+    for v in sorted(members):
+        for l in sim.groups(v):
+            if v < l and l in members:
+                heapq.heappush(heap, (score(v, l), v, l, 0, 0))
+    while heap:
+        _, i, j, vi, vj = heapq.heappop(heap)
+        if i not in members or j not in members or version[i] != vi or version[j] != vj:
+            continue
+        k = nxt
+        nxt += 1
+        ops.append(("C", i, j, k))
+        sim.contract(i, j, k)
+        members.discard(i)
+        members.discard(j)
+        members.add(k)
+        if on_contract is not None:
+            on_contract(i, j, k)
+        version[k] = 0
+        for l in sorted(sim.groups(k)):
+            ops.append(("S", k, l))
+            if sim.compress(k, l, chig) and l in version:
+                version[l] += 1
+        push_around(k)
+        for l in sim.groups(k):
+            if l in members:
+                push_around(l)
+    return nxt
+
+
 def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int,
            seed: int = 0, temperature: float = 0.0, w_new: float = 1.0, w_old: float = 0.0,
            w_inputs: float = -1.0, w_subgraph: float = 0.0, w_centrality: float = 0.0,
@@ -468,10 +520,8 @@ def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: in
     adj0 = [sorted(set(o for b in net_bonds[v] for o in sim.owner[b] if o != v)) for v in range(n)]
     cent = {v: float(c) for v, c in enumerate(centrality(n, adj0))} if w_centrality else {v: 0.0 for v in range(n)}
     sub = {v: 1 for v in range(n)}
-    pairs: List[Tuple[int, int]] = []
     ops: List[tuple] = []
     nxt = n
-    version: Dict[int, int] = {v: 0 for v in range(n)}
 
     def score(i: int, j: int) -> float:
         before, after = sim.contract_sizes(i, j, chig)
@@ -483,36 +533,11 @@ def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: in
             s += temperature * float(-math.log(-math.log(rng.uniform(1e-12, 1.0))))
         return s
 
-    heap: List[Tuple[float, int, int, int, int]] = []
-
-    def push_around(t: int) -> None:
-        for l in sim.groups(t):
-            a, b = (t, l) if t < l else (l, t)
-            heapq.heappush(heap, (score(a, b), a, b, version[a], version[b]))
-
-    for v in range(n):
-        for l in sim.groups(v):
-            if v < l:
-                heapq.heappush(heap, (score(v, l), v, l, 0, 0))
-    while heap:
-        _, i, j, vi, vj = heapq.heappop(heap)
-        if i not in sim.bonds or j not in sim.bonds or version[i] != vi or version[j] != vj:
-            continue
-        k = nxt
-        nxt += 1
-        ops.append(("C", i, j, k))
-        pairs.append((i, j))
-        sim.contract(i, j, k)
+    def on_contract(i: int, j: int, k: int) -> None:
         sub[k] = sub[i] + sub[j]
         cent[k] = {"min": min, "max": max}.get(centrality_prop, lambda a, b: 0.5 * (a + b))(cent[i], cent[j])
-        version[k] = 0
-        for l in sorted(sim.groups(k)):
-            ops.append(("S", k, l))
-            if sim.compress(k, l, chig):
-                version[l] += 1
-        push_around(k)
-        for l in sim.groups(k):
-            push_around(l)
+
+    nxt = _greedy_loop(sim, set(range(n)), chig, score, ops, nxt, on_contract)
     live = sorted(sim.bonds)
     acc = live[0] if live else None
     for t in live[1:]:
@@ -522,6 +547,82 @@ def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: in
         nxt += 1
     if policy != "early":
         raise ValueError("greedy emits early compression")
+    return Tree(n, ops)
+
+
+# ---------------------------------------------------------------------------
+# Agglom builder
+
+
+def agglom(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int, K: int = 8,
+           imbalance: float = 0.1, mode: str = "recursive", weight: str = "log",
+           chi_agglom: Optional[int] = None, seed: int = 0) -> Tree:
+    """Agglom ordered tree (SI "Agglom"): cut the live tensors into about N / K
+    balanced communities (``partition.partition``, mode "recursive" or
+    "direct", sizes within 1 +- imbalance of N / parts, each bond weighted by
+    1 ("const") or by log2 of its simulated size ("log")), contract each
+    community to one tensor with the Greedy builder's default score (early
+    compressions simulated at chi_agglom, default chi), compress the bonds
+    between the new community tensors, and repeat on that coarse network
+    until one tensor is left.
+
+    Order: level by level (so contractions come in order of sub-graph size),
+    and within a level the communities in ascending order of the average
+    centrality of the input tensors they hold (the periphery first).  A
+    community that is not connected inside is joined by outer products.
+    """
+    from .partition import partition
+    if K < 2:
+        raise ValueError("agglom needs a community size K >= 2")
+    if weight not in ("const", "log"):
+        raise ValueError(f"unknown edge weighting {weight!r}")
+    chia = chi_agglom or chi
+    rng = np.random.default_rng(seed)
+    n = len(net_bonds)
+    sim = _Sim(net_bonds, bond_dims)
+    adj0 = [sorted(set(o for b in net_bonds[v] for o in sim.owner[b] if o != v)) for v in range(n)]
+    c0 = centrality(n, adj0) if n > 1 else np.zeros(n)
+    csum = {v: float(c0[v]) for v in range(n)}
+    cnt = {v: 1 for v in range(n)}
+    ops: List[tuple] = []
+    nxt = n
+
+    def score(i: int, j: int) -> float:
+        _, after = sim.contract_sizes(i, j, chia)
+        return after - (sim.log2size(i) + sim.log2size(j))
+
+    def on_contract(i: int, j: int, k: int) -> None:
+        csum[k] = csum.pop(i) + csum.pop(j)
+        cnt[k] = cnt.pop(i) + cnt.pop(j)
+
+    while len(sim.bonds) > 1:
+        live = sorted(sim.bonds)
+        p = min(max(1, int(round(len(live) / K))), max(1, len(live) // 2))
+        w: Dict[Tuple[int, int], float] = {}
+        for t in live:
+            for l, bl in sim.groups(t).items():
+                if t < l:
+                    w[(t, l)] = sum(1.0 if weight == "const" else max(math.log2(sim.dim[b]), 1e-3) for b in bl)
+        parts = partition(live, w, p, imbalance, mode, seed=int(rng.integers(2 ** 31)))
+        parts.sort(key=lambda part: (sum(csum[v] for v in part) / sum(cnt[v] for v in part), part[0]))
+        new = []
+        for part in parts:
+            members = set(part)
+            nxt = _greedy_loop(sim, members, chia, score, ops, nxt, on_contract)
+            rest = sorted(members)
+            acc = rest[0]
+            for t in rest[1:]:
+                ops.append(("C", acc, t, nxt))
+                sim.contract(acc, t, nxt)
+                on_contract(acc, t, nxt)
+                acc = nxt
+                nxt += 1
+            new.append(acc)
+        for t in sorted(new):
+            for l in sorted(sim.groups(t)):
+                if t < l:
+                    ops.append(("S", t, l))
+                    sim.compress(t, l, chia)
     return Tree(n, ops)
 
 
@@ -609,7 +710,8 @@ def hyper_search(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], c
     builder "span": the feature priority order, the signs, the start node
     (central / peripheral), a temperature in {0, 0.5, 2} and the compression
     policy (early / late).  builder "greedy": the score weights, the
-    temperature and chi_greedy.  objective: a key of trace_cost's result
+    temperature and chi_greedy.  builder "agglom": the community size, the
+    imbalance, the partition mode, the edge weighting and chi_agglom.  objective: a key of trace_cost's result
     ("total" = the SI's cost C, "peak" = largest intermediate, ...).
     Returns (best tree, its parameters, its objective value, [objective of each trial]).
     """
@@ -641,6 +743,15 @@ def hyper_search(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], c
                           centrality_prop=str(rng.choice(["mean", "min", "max"])),
                           chi_greedy=int(rng.choice([chi, chi, 2 * chi, max(1, chi // 2)])))
             tree = greedy(net_bonds, bond_dims, chi, **params)
+        elif builder == "agglom":
+            # the SI's Agglom dimensions: community size K, imbalance, partition
+            # mode, edge weighting and the simulated chi_agglom
+            params = dict(seed=trial, K=int(rng.choice([2, 3, 4, 6, 8, 12, 16, 24, 32])),
+                          imbalance=float(rng.choice([0.01, 0.05, 0.1, 0.2, 0.4])),
+                          mode=str(rng.choice(["recursive", "direct"])),
+                          weight=str(rng.choice(["const", "log"])),
+                          chi_agglom=int(rng.choice([chi, max(1, chi // 2), 2 * chi])))
+            tree = agglom(net_bonds, bond_dims, chi, **params)
         else:
             raise ValueError(builder)
         cost = float(trace_cost(net_bonds, bond_dims, tree, chi)[objective])
