@@ -218,7 +218,9 @@ def partition(nodes: Sequence[int], w: Dict[Tuple[int, int], float], n_parts: in
     """Split ``nodes`` into ``n_parts`` parts of near-equal size, few cut edges.
 
     w[(a, b)]: weight of the edge between nodes a and b (summed if given both
-    ways).  Returns lists of node ids; every node is in exactly one part.
+    ways).  Returns lists of node ids; every node is in exactly one part.  A
+    recursive split can end with fewer parts than asked when a refinement
+    move leaves one side with fewer nodes than parts; no part is empty.
     """
     nodes = list(nodes)
     n_parts = max(1, min(int(n_parts), len(nodes)))
