@@ -17,6 +17,9 @@ sweep or every seed of a random ensemble.  Generators:
 * ``agglom``: the Agglom builder of the SI (balanced communities from a graph
   partitioner, Greedy inside each, compression between them, repeated on
   the coarse network).
+* ``branch_and_bound``: depth-first branch and bound over contraction
+  sequences (the SI's exhaustive search for small graphs, or a refinement of
+  a given tree when stopped early).
 * ``hyper_search``: random search over any builder's parameters scored by
   the cost tracer (Algorithm 3).
 
@@ -630,69 +633,182 @@ def agglom(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: in
 # tracing (Sec. "Tree cost functions" of the SI)
 
 
-def trace_cost(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], tree: Tree, chi: int) -> Dict[str, float]:
-    """Walk the tree for one chi and count the paper's cost units
+class _Tracer:
+    """Running cost of an ordered tree, one op at a time (the SI's cost units)
 
     contraction (m, n) x (n, k): m n k;  QR of (m, n), m >= n: 2 m n^2 - 2/3 n^3;
     SVD of (m, n), m >= n: 4 m n^2 - 4/3 n^3;  plus peak live memory M (elements)
     and the largest tensor W.  QR here is of each side of a compression
-    (D_A x D_AB and D_AB x D_B), the SVD of the r_A x r_B core.
+    (D_A x D_AB and D_AB x D_B), the SVD of the r_A x r_B core.  ``copy()``
+    forks the state (for tree searches that branch).
     """
-    sim = _Sim(net_bonds, bond_dims)
-    cost_c = cost_qr = cost_svd = 0.0
-    sizes = {t: 2.0 ** sim.log2size(t) for t in sim.bonds}
-    live = sum(sizes.values())
-    peak = live
-    wmax = max(sizes.values()) if sizes else 0.0
-    n_comp = 0
 
-    def qr(m: float, nn: float) -> float:
+    def __init__(self, net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int):
+        self.sim = _Sim(net_bonds, bond_dims)
+        self.chi = chi
+        self.cost_c = self.cost_qr = self.cost_svd = 0.0
+        self.sizes = {t: 2.0 ** self.sim.log2size(t) for t in self.sim.bonds}
+        self.live = sum(self.sizes.values())
+        self.peak = self.live
+        self.wmax = max(self.sizes.values()) if self.sizes else 0.0
+        self.n_comp = 0
+
+    def copy(self) -> "_Tracer":
+        t = _Tracer.__new__(_Tracer)
+        t.__dict__.update(self.__dict__)
+        sim = _Sim.__new__(_Sim)
+        sim.bonds = {k: list(v) for k, v in self.sim.bonds.items()}
+        sim.dim = dict(self.sim.dim)
+        sim.owner = {k: list(v) for k, v in self.sim.owner.items()}
+        sim.next_bond = self.sim.next_bond
+        t.sim = sim
+        t.sizes = dict(self.sizes)
+        return t
+
+    @staticmethod
+    def _qr(m: float, nn: float) -> float:
         if m < nn:
             m, nn = nn, m
         return 2 * m * nn * nn - 2.0 / 3.0 * nn ** 3
 
-    def svd(m: float, nn: float) -> float:
+    @staticmethod
+    def _svd(m: float, nn: float) -> float:
         if m < nn:
             m, nn = nn, m
         return 4 * m * nn * nn - 4.0 / 3.0 * nn ** 3
 
-    for op in tree.ops:
+    def contract(self, i: int, j: int, k: int) -> None:
+        sim, sizes = self.sim, self.sizes
+        sh = [b for b in sim.bonds[i] if b in set(sim.bonds[j])]
+        dab = 2.0 ** sum(math.log2(sim.dim[b]) for b in sh)
+        m = sizes[i] / dab
+        nn = sizes[j] / dab
+        self.cost_c += m * dab * nn
+        sim.contract(i, j, k)
+        sizes[k] = m * nn
+        self.live += sizes[k]
+        self.peak = max(self.peak, self.live)
+        self.live -= sizes.pop(i) + sizes.pop(j)
+        self.wmax = max(self.wmax, sizes[k])
+
+    def compress(self, i: int, j: int) -> None:
+        sim, sizes, chi = self.sim, self.sizes, self.chi
+        sh = [b for b in sim.bonds[i] if b in set(sim.bonds[j])]
+        dab = 2.0 ** sum(math.log2(sim.dim[b]) for b in sh)
+        if dab <= chi:
+            return
+        da = sizes[i] / dab
+        db = sizes[j] / dab
+        ra, rb = min(da, dab), min(db, dab)
+        self.cost_qr += self._qr(da, dab) + self._qr(dab, db)
+        self.cost_c += ra * dab * rb
+        self.cost_svd += self._svd(ra, rb)
+        kk = min(chi, da, db)
+        self.cost_c += da * ra * kk + kk * rb * db
+        sim.compress(i, j, chi)
+        self.live -= sizes[i] + sizes[j]
+        sizes[i] = da * kk
+        sizes[j] = kk * db
+        self.live += sizes[i] + sizes[j]
+        self.n_comp += 1
+
+    def step(self, op: tuple) -> None:
         if op[0] == "C":
-            _, i, j, k = op
-            sh = [b for b in sim.bonds[i] if b in set(sim.bonds[j])]
-            dab = 2.0 ** sum(math.log2(sim.dim[b]) for b in sh)
-            m = sizes[i] / dab
-            nn = sizes[j] / dab
-            cost_c += m * dab * nn
-            sim.contract(i, j, k)
-            sizes[k] = m * nn
-            live += sizes[k]
-            peak = max(peak, live)
-            live -= sizes.pop(i) + sizes.pop(j)
-            wmax = max(wmax, sizes[k])
+            self.contract(op[1], op[2], op[3])
         else:
-            _, i, j = op
-            sh = [b for b in sim.bonds[i] if b in set(sim.bonds[j])]
-            dab = 2.0 ** sum(math.log2(sim.dim[b]) for b in sh)
-            if dab <= chi:
+            self.compress(op[1], op[2])
+
+    def result(self) -> Dict[str, float]:
+        return {"contract": self.cost_c, "qr": self.cost_qr, "svd": self.cost_svd,
+                "total": self.cost_c + self.cost_qr + self.cost_svd, "peak": self.peak, "wmax": self.wmax,
+                "compressions": self.n_comp}
+
+
+def trace_cost(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], tree: Tree, chi: int) -> Dict[str, float]:
+    """Walk the tree for one chi and count the paper's cost units (see _Tracer):
+    contraction, QR and SVD costs, their total C, the peak live memory M and
+    the largest tensor W, and the number of compressions that fire."""
+    tr_ = _Tracer(net_bonds, bond_dims, chi)
+    for op in tree.ops:
+        tr_.step(op)
+    return tr_.result()
+
+
+# ---------------------------------------------------------------------------
+# branch and bound (SI "Branch & bound approximate contraction tree")
+
+
+def branch_and_bound(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int,
+                     objective: str = "total", max_nodes: int = 200000,
+                     upper: Optional[Tree] = None) -> Tuple[Tree, float, bool]:
+    """Depth-first branch and bound over contraction sequences with early
+    compression (each new tensor compressed against every neighbour, as in
+    ``from_pairs(..., "early")``), scored by the tracer's ``objective``
+    ("total" = the cost C, "peak" = the peak memory M, or "wmax").
+
+    A branch contracts one pair of adjacent live tensors (any pair when none
+    is adjacent); children are explored lowest score first, so a complete
+    tree, and with it an upper bound, is reached early.  Both scores only
+    grow along a branch, so a branch whose score already reaches the best
+    complete tree's is dropped: a search that ends within ``max_nodes``
+    visited states returns an optimal tree of this space.  ``upper`` (a tree
+    of the same network, e.g. a Greedy tree) seeds the bound, so an
+    interrupted search refines it.  Returns (tree, its score, complete).
+    """
+    if objective not in ("total", "peak", "wmax"):
+        raise ValueError(f"unknown objective {objective!r}")
+    n = len(net_bonds)
+
+    def score(t: _Tracer) -> float:
+        if objective == "total":
+            return t.cost_c + t.cost_qr + t.cost_svd
+        return t.peak if objective == "peak" else t.wmax
+
+    best_score, best_tree, best_path = math.inf, None, None
+    if upper is not None:
+        best_score = trace_cost(net_bonds, bond_dims, upper, chi)[objective]
+        best_tree = upper
+    visited = 0
+    complete = True
+
+    def dfs(t: _Tracer, path: List[Tuple[int, int]], nxt: int) -> None:
+        nonlocal best_score, best_path, visited, complete
+        if visited >= max_nodes:
+            complete = False
+            return
+        visited += 1
+        live = sorted(t.sim.bonds)
+        if len(live) <= 1:
+            sc = score(t)
+            if sc < best_score:
+                best_score, best_path = sc, list(path)
+            return
+        pairs = sorted({(min(i, l), max(i, l)) for i in live for l in t.sim.groups(i)})
+        if not pairs:
+            pairs = [(a, b) for x, a in enumerate(live) for b in live[x + 1:]]
+        children = []
+        for i, j in pairs:
+            c = t.copy()
+            c.contract(i, j, nxt)
+            for l in sorted(c.sim.groups(nxt)):
+                c.compress(nxt, l)
+            sc = score(c)
+            if sc < best_score:
+                children.append((sc, i, j, c))
+        children.sort(key=lambda x: (x[0], x[1], x[2]))
+        for sc, i, j, c in children:
+            if sc >= best_score:
                 continue
-            da = sizes[i] / dab
-            db = sizes[j] / dab
-            ra, rb = min(da, dab), min(db, dab)
-            cost_qr += qr(da, dab) + qr(dab, db)
-            cost_c += ra * dab * rb
-            cost_svd += svd(ra, rb)
-            kk = min(chi, da, db)
-            cost_c += da * ra * kk + kk * rb * db
-            sim.compress(i, j, chi)
-            live -= sizes[i] + sizes[j]
-            sizes[i] = da * kk
-            sizes[j] = kk * db
-            live += sizes[i] + sizes[j]
-            n_comp += 1
-    return {"contract": cost_c, "qr": cost_qr, "svd": cost_svd,
-            "total": cost_c + cost_qr + cost_svd, "peak": peak, "wmax": wmax,
-            "compressions": n_comp}
+            path.append((i, j))
+            dfs(c, path, nxt + 1)
+            path.pop()
+
+    dfs(_Tracer(net_bonds, bond_dims, chi), [], n)
+    if best_path is not None:
+        best_tree = from_pairs(net_bonds, best_path, "early")
+    if best_tree is None:
+        raise RuntimeError("branch and bound found no tree within max_nodes")
+    return best_tree, best_score, complete
 
 
 # ---------------------------------------------------------------------------
