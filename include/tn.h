@@ -142,7 +142,10 @@ typedef struct {
  *                      fill the SMs another leaves idle; 0 or 1 (default):
  *                      one batch.  Results may differ in the last bits from
  *                      the unsplit batch (launch shapes depend on the batch
- *                      size).  Requires sequential_groups = 0. */
+ *                      size).  Requires sequential_groups = 0.  On the
+ *                      8-instance 32x32 D=4 chi=64 batch it ran slower at
+ *                      k = 2 and 4 (the sub-batches' cluster launches
+ *                      compete for the same GPCs). */
 typedef struct {
   int32_t struct_size;
   int32_t graph_mode;

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <algorithm>
 #include <fstream>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <sstream>
@@ -289,12 +290,13 @@ bool same_group(const tn_ctx* c, int a, int b) {
 
 int ensure_scratch(tn_ctx* c, int batch) {
   if (c->scratch_batch >= batch) return TN_OK;
-  cudaFree(c->expo);
-  cudaFree(c->status);
-  cudaFree(c->jac_ws);
-  cudaFree(c->maxbits);
-  cudaFree(c->out_log);
-  cudaFree(c->out_sign);
+  // null every pointer once freed: a failed allocation below must not leave
+  // one that the next call (or tn_destroy) would free a second time
+  for (void** p : {(void**)&c->expo, (void**)&c->status, (void**)&c->jac_ws, (void**)&c->maxbits,
+                   (void**)&c->out_log, (void**)&c->out_sign}) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
   c->scratch_batch = 0;
   if (cudaMalloc(&c->expo, sizeof(long long) * batch) != cudaSuccess ||
       cudaMalloc(&c->status, sizeof(int) * batch) != cudaSuccess ||
@@ -595,14 +597,11 @@ int run_groups_concurrent(tn_ctx* c, const std::vector<const tnp::Plan*>& plans,
   if ((e = ensure(&M.inbuf, &M.inbuf_bytes, sizeof(double) * (size_t)i_tot)) != cudaSuccess)
     return fail(c, TN_ENOMEM, "input buffer allocation failed");
   if (M.cap_inst < o_tot || M.cap_groups < G) {
-    cudaFree(M.expo);
-    cudaFree(M.status);
-    cudaFree(M.jac_ws);
-    cudaFree(M.maxbits);
-    cudaFree(M.out_log);
-    cudaFree(M.out_sign);
-    cudaFree(M.tc_err);
-    M.expo = nullptr;
+    for (void** p : {(void**)&M.expo, (void**)&M.status, (void**)&M.jac_ws, (void**)&M.maxbits,
+                     (void**)&M.out_log, (void**)&M.out_sign, (void**)&M.tc_err}) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
     M.cap_inst = M.cap_groups = 0;
     const size_t n = (size_t)o_tot;
     if (cudaMalloc(&M.expo, sizeof(long long) * n) != cudaSuccess ||
