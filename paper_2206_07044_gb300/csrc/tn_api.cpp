@@ -1353,7 +1353,7 @@ int tn_autotune(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, i
     for (const auto& w : work)
       if (w.first.kernel != tnk::TK_GEMM64 && w.first.kernel != tnk::TK_GEMMTC) keys.push_back(w.first);
     double covered = 0.0;
-    for (const auto& gk : gemms) {  // the GEMM shapes that carry 98% of the GEMM flops, at most 24
+    for (const auto& gk : gemms) {  // the GEMM shapes that carry 98% of the GEMM flops (64 shapes at most in all)
       if (covered >= 0.98 * gemm_total || (int)keys.size() >= 64) break;
       keys.push_back(gk.second);
       covered += gk.first;
@@ -1368,17 +1368,24 @@ int tn_autotune(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, i
         elems = (size_t)m * n, aux = (size_t)n * n + n;
       if (key.kernel == tnk::TK_GEMM64 || key.kernel == tnk::TK_GEMMTC)
         elems = (size_t)m * k + (size_t)k * n, aux = (size_t)m * n;
-      double* d_in = nullptr;
-      double* d_aux = nullptr;
-      void* d_ws = nullptr;
+      struct Scratch {  // freed on every exit from this shape's iteration
+        double* in = nullptr;
+        double* aux = nullptr;
+        void* ws = nullptr;
+        ~Scratch() {
+          cudaFree(in);
+          cudaFree(aux);
+          cudaFree(ws);
+        }
+      } sc;
+      double*& d_in = sc.in;
+      double*& d_aux = sc.aux;
+      void*& d_ws = sc.ws;
       size_t ws_bytes = 0;
       if (key.kernel == tnk::TK_GEMMTC) ws_bytes = tnk::gemm_tc_workspace_bytes(m, n, k, prec == 1 ? 0 : (prec == 2 ? 1 : 2), batch);
       if (cudaMalloc(&d_in, sizeof(double) * elems * batch) != cudaSuccess ||
           cudaMalloc(&d_aux, sizeof(double) * aux * batch) != cudaSuccess ||
           (ws_bytes && cudaMalloc(&d_ws, ws_bytes) != cudaSuccess)) {
-        cudaFree(d_in);
-        cudaFree(d_aux);
-        cudaFree(d_ws);
         cudaGetLastError();
         return fail(c, TN_ENOMEM, "autotune scratch allocation failed");
       }
@@ -1446,9 +1453,6 @@ int tn_autotune(tn_ctx* c, int n_inst, const int* inst_ids, int chi, int prec, i
       }
       tnk::tune_set(key.kernel, m, n, k, batch, best > 0 ? best : saved);
       if (best > 0) ++tuned;
-      cudaFree(d_in);
-      cudaFree(d_aux);
-      cudaFree(d_ws);
       // the scratch runs may have flagged statuses (capped sweeps): clear them
       cudaMemsetAsync(c->status, 0, sizeof(int) * batch, s);
       cudaMemsetAsync(c->tc_err, 0, sizeof(int), s);
