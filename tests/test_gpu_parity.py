@@ -125,26 +125,6 @@ def test_searched_trees_on_16x16_d4_chi64(ctx, builder):
     assert want.compressions > 50
 
 
-@pytest.mark.parametrize("case", ["6x7_d3", "ising_8x8_direct", "dimers_n40"])
-def test_agglom_trees_against_the_oracle(ctx, case):
-    """Agglom trees (SI "Agglom": balanced communities, Greedy inside, compression
-    between them, repeated) executed by the library against the oracle."""
-    if case == "6x7_d3":
-        n, e = nw.square_lattice(6, 7)
-        net, chi = nw.random_network(n, e, 3, seed=12), 6
-        t = tr.agglom(net.bonds, net.bond_dims, chi, K=4)
-    elif case == "ising_8x8_direct":
-        n, e = nw.square_lattice(8, 8)
-        net, chi = nw.ising_network(n, e, 0.44), 4
-        t = tr.agglom(net.bonds, net.bond_dims, chi, K=4, mode="direct")
-    else:
-        n, e = nw.random_regular_graph(40, 3, seed=3)
-        net, chi = nw.dimer_network(n, e), 8
-        t = tr.agglom(net.bonds, net.bond_dims, chi, K=4)
-    got, want = check(ctx, net, t, chi)
-    assert want.compressions > 0
-
-
 def test_cdl_exact_at_chi_4(ctx):
     net = nw.cdl_network(6, 6, 2)
     got, _ = gpu_run(ctx, net, tr.boundary_rows(6, 6), 4)

@@ -14,12 +14,6 @@ sweep or every seed of a random ensemble.  Generators:
   Gumbel noise term), simulated with chi_greedy.
 * ``span``: the Span builder (a spanning tree grown by Algorithm 2,
   contracted leaves inwards).
-* ``agglom``: the Agglom builder of the SI (balanced communities from a graph
-  partitioner, Greedy inside each, compression between them, repeated on
-  the coarse network).
-* ``branch_and_bound``: depth-first branch and bound over contraction
-  sequences (the SI's exhaustive search for small graphs, or a refinement of
-  a given tree when stopped early).
 * ``hyper_search``: random search over any builder's parameters scored by
   the cost tracer (Algorithm 3).
 
@@ -554,82 +548,6 @@ def greedy(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: in
 
 
 # ---------------------------------------------------------------------------
-# Agglom builder
-
-
-def agglom(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int, K: int = 8,
-           imbalance: float = 0.1, mode: str = "recursive", weight: str = "log",
-           chi_agglom: Optional[int] = None, seed: int = 0) -> Tree:
-    """Agglom ordered tree (SI "Agglom"): cut the live tensors into about N / K
-    balanced communities (``partition.partition``, mode "recursive" or
-    "direct", sizes within 1 +- imbalance of N / parts, each bond weighted by
-    1 ("const") or by log2 of its simulated size ("log")), contract each
-    community to one tensor with the Greedy builder's default score (early
-    compressions simulated at chi_agglom, default chi), compress the bonds
-    between the new community tensors, and repeat on that coarse network
-    until one tensor is left.
-
-    Order: level by level (so contractions come in order of sub-graph size),
-    and within a level the communities in ascending order of the average
-    centrality of the input tensors they hold (the periphery first).  A
-    community that is not connected inside is joined by outer products.
-    """
-    from .partition import partition
-    if K < 2:
-        raise ValueError("agglom needs a community size K >= 2")
-    if weight not in ("const", "log"):
-        raise ValueError(f"unknown edge weighting {weight!r}")
-    chia = chi_agglom or chi
-    rng = np.random.default_rng(seed)
-    n = len(net_bonds)
-    sim = _Sim(net_bonds, bond_dims)
-    adj0 = [sorted(set(o for b in net_bonds[v] for o in sim.owner[b] if o != v)) for v in range(n)]
-    c0 = centrality(n, adj0) if n > 1 else np.zeros(n)
-    csum = {v: float(c0[v]) for v in range(n)}
-    cnt = {v: 1 for v in range(n)}
-    ops: List[tuple] = []
-    nxt = n
-
-    def score(i: int, j: int) -> float:
-        _, after = sim.contract_sizes(i, j, chia)
-        return after - (sim.log2size(i) + sim.log2size(j))
-
-    def on_contract(i: int, j: int, k: int) -> None:
-        csum[k] = csum.pop(i) + csum.pop(j)
-        cnt[k] = cnt.pop(i) + cnt.pop(j)
-
-    while len(sim.bonds) > 1:
-        live = sorted(sim.bonds)
-        p = min(max(1, int(round(len(live) / K))), max(1, len(live) // 2))
-        w: Dict[Tuple[int, int], float] = {}
-        for t in live:
-            for l, bl in sim.groups(t).items():
-                if t < l:
-                    w[(t, l)] = sum(1.0 if weight == "const" else max(math.log2(sim.dim[b]), 1e-3) for b in bl)
-        parts = partition(live, w, p, imbalance, mode, seed=int(rng.integers(2 ** 31)))
-        parts.sort(key=lambda part: (sum(csum[v] for v in part) / sum(cnt[v] for v in part), part[0]))
-        new = []
-        for part in parts:
-            members = set(part)
-            nxt = _greedy_loop(sim, members, chia, score, ops, nxt, on_contract)
-            rest = sorted(members)
-            acc = rest[0]
-            for t in rest[1:]:
-                ops.append(("C", acc, t, nxt))
-                sim.contract(acc, t, nxt)
-                on_contract(acc, t, nxt)
-                acc = nxt
-                nxt += 1
-            new.append(acc)
-        for t in sorted(new):
-            for l in sorted(sim.groups(t)):
-                if t < l:
-                    ops.append(("S", t, l))
-                    sim.compress(t, l, chia)
-    return Tree(n, ops)
-
-
-# ---------------------------------------------------------------------------
 # tracing (Sec. "Tree cost functions" of the SI)
 
 
@@ -639,8 +557,7 @@ class _Tracer:
     contraction (m, n) x (n, k): m n k;  QR of (m, n), m >= n: 2 m n^2 - 2/3 n^3;
     SVD of (m, n), m >= n: 4 m n^2 - 4/3 n^3;  plus peak live memory M (elements)
     and the largest tensor W.  QR here is of each side of a compression
-    (D_A x D_AB and D_AB x D_B), the SVD of the r_A x r_B core.  ``copy()``
-    forks the state (for tree searches that branch).
+    (D_A x D_AB and D_AB x D_B), the SVD of the r_A x r_B core.
     """
 
     def __init__(self, net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int):
@@ -652,18 +569,6 @@ class _Tracer:
         self.peak = self.live
         self.wmax = max(self.sizes.values()) if self.sizes else 0.0
         self.n_comp = 0
-
-    def copy(self) -> "_Tracer":
-        t = _Tracer.__new__(_Tracer)
-        t.__dict__.update(self.__dict__)
-        sim = _Sim.__new__(_Sim)
-        sim.bonds = {k: list(v) for k, v in self.sim.bonds.items()}
-        sim.dim = dict(self.sim.dim)
-        sim.owner = {k: list(v) for k, v in self.sim.owner.items()}
-        sim.next_bond = self.sim.next_bond
-        t.sim = sim
-        t.sizes = dict(self.sizes)
-        return t
 
     @staticmethod
     def _qr(m: float, nn: float) -> float:
@@ -735,83 +640,6 @@ def trace_cost(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], tre
 
 
 # ---------------------------------------------------------------------------
-# branch and bound (SI "Branch & bound approximate contraction tree")
-
-
-def branch_and_bound(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], chi: int,
-                     objective: str = "total", max_nodes: int = 200000,
-                     upper: Optional[Tree] = None) -> Tuple[Tree, float, bool]:
-    """Depth-first branch and bound over contraction sequences with early
-    compression (each new tensor compressed against every neighbour, as in
-    ``from_pairs(..., "early")``), scored by the tracer's ``objective``
-    ("total" = the cost C, "peak" = the peak memory M, or "wmax").
-
-    A branch contracts one pair of adjacent live tensors (any pair when none
-    is adjacent); children are explored lowest score first, so a complete
-    tree, and with it an upper bound, is reached early.  Both scores only
-    grow along a branch, so a branch whose score already reaches the best
-    complete tree's is dropped: a search that ends within ``max_nodes``
-    visited states returns an optimal tree of this space.  ``upper`` (a tree
-    of the same network, e.g. a Greedy tree) seeds the bound, so an
-    interrupted search refines it.  Returns (tree, its score, complete).
-    """
-    if objective not in ("total", "peak", "wmax"):
-        raise ValueError(f"unknown objective {objective!r}")
-    n = len(net_bonds)
-
-    def score(t: _Tracer) -> float:
-        if objective == "total":
-            return t.cost_c + t.cost_qr + t.cost_svd
-        return t.peak if objective == "peak" else t.wmax
-
-    best_score, best_tree, best_path = math.inf, None, None
-    if upper is not None:
-        best_score = trace_cost(net_bonds, bond_dims, upper, chi)[objective]
-        best_tree = upper
-    visited = 0
-    complete = True
-
-    def dfs(t: _Tracer, path: List[Tuple[int, int]], nxt: int) -> None:
-        nonlocal best_score, best_path, visited, complete
-        if visited >= max_nodes:
-            complete = False
-            return
-        visited += 1
-        live = sorted(t.sim.bonds)
-        if len(live) <= 1:
-            sc = score(t)
-            if sc < best_score:
-                best_score, best_path = sc, list(path)
-            return
-        pairs = sorted({(min(i, l), max(i, l)) for i in live for l in t.sim.groups(i)})
-        if not pairs:
-            pairs = [(a, b) for x, a in enumerate(live) for b in live[x + 1:]]
-        children = []
-        for i, j in pairs:
-            c = t.copy()
-            c.contract(i, j, nxt)
-            for l in sorted(c.sim.groups(nxt)):
-                c.compress(nxt, l)
-            sc = score(c)
-            if sc < best_score:
-                children.append((sc, i, j, c))
-        children.sort(key=lambda x: (x[0], x[1], x[2]))
-        for sc, i, j, c in children:
-            if sc >= best_score:
-                continue
-            path.append((i, j))
-            dfs(c, path, nxt + 1)
-            path.pop()
-
-    dfs(_Tracer(net_bonds, bond_dims, chi), [], n)
-    if best_path is not None:
-        best_tree = from_pairs(net_bonds, best_path, "early")
-    if best_tree is None:
-        raise RuntimeError("branch and bound found no tree within max_nodes")
-    return best_tree, best_score, complete
-
-
-# ---------------------------------------------------------------------------
 # hyper-optimization loop (Algorithm 3) by random search
 
 SPAN_FEATURES = ("distance", "connectivity", "ndim", "centrality")
@@ -826,8 +654,7 @@ def hyper_search(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], c
     builder "span": the feature priority order, the signs, the start node
     (central / peripheral), a temperature in {0, 0.5, 2} and the compression
     policy (early / late).  builder "greedy": the score weights, the
-    temperature and chi_greedy.  builder "agglom": the community size, the
-    imbalance, the partition mode, the edge weighting and chi_agglom.  objective: a key of trace_cost's result
+    temperature and chi_greedy.  objective: a key of trace_cost's result
     ("total" = the SI's cost C, "peak" = largest intermediate, ...).
     Returns (best tree, its parameters, its objective value, [objective of each trial]).
     """
@@ -859,15 +686,6 @@ def hyper_search(net_bonds: Sequence[Sequence[int]], bond_dims: Sequence[int], c
                           centrality_prop=str(rng.choice(["mean", "min", "max"])),
                           chi_greedy=int(rng.choice([chi, chi, 2 * chi, max(1, chi // 2)])))
             tree = greedy(net_bonds, bond_dims, chi, **params)
-        elif builder == "agglom":
-            # the SI's Agglom dimensions: community size K, imbalance, partition
-            # mode, edge weighting and the simulated chi_agglom
-            params = dict(seed=trial, K=int(rng.choice([2, 3, 4, 6, 8, 12, 16, 24, 32])),
-                          imbalance=float(rng.choice([0.01, 0.05, 0.1, 0.2, 0.4])),
-                          mode=str(rng.choice(["recursive", "direct"])),
-                          weight=str(rng.choice(["const", "log"])),
-                          chi_agglom=int(rng.choice([chi, max(1, chi // 2), 2 * chi])))
-            tree = agglom(net_bonds, bond_dims, chi, **params)
         else:
             raise ValueError(builder)
         cost = float(trace_cost(net_bonds, bond_dims, tree, chi)[objective])
